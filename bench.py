@@ -1,0 +1,326 @@
+"""Throughput of the per-sweep SCO hot path on GB300.
+
+One step = one MC step of the whole path at n_sw = 1: switch every dipolar pair (step (A)),
+compact the survivors into the CSR graph, Kuhn-Wattenhofer colouring and colour classes,
+and one colour-class Metropolis sweep (every site updated once).  Metric: spin updates/s
+= N * steps / time.  Workload: L = 2304 (N = 5,308,416) open lattice, J = 0, D = 1,
+T = 0.6 D, seed 0, spins uniform on the sphere (synthetic, like the paper's lattices).
+
+Prints one JSON line.  Under torchrun every rank runs its own replica (seed + rank, no
+collective on the data path; weak scaling); rank 0 reports the max time over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin updates/s (switch+colour+sweep) at L=2304; FP32-guarded vs FP64; % HBM"
+UNIT = "spin updates/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=2304)
+    ap.add_argument("--T", type=float, default=0.6)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-guarded arm")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--cpu-L", type=int, default=2304, help="lattice of the oracle sample")
+    ap.add_argument("--ref-L", type=int, default=384, help="lattice of one reference-arm step")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def algorithmic_bytes(k, M):
+    """Bytes per spin update that each phase must move at least once:
+    switch + CSR 40 + 16k, colouring + classes M (4 + 2k) + 12, sweep 60 + 8k."""
+    return {"switch": 40 + 16 * k, "colour": M * (4 + 2 * k) + 12, "sweep": 60 + 8 * k}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1503_03295_gb300 as sco
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    sh = stream.cuda_stream
+    L = args.L
+    N = L * L
+
+    def lattice(prec):
+        return sco.Lattice(sco.make_params(L, T=args.T, seed=args.seed + rank, precision=prec),
+                           stream=sh)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(lat, K, W, timing=False):
+        lat.sweep(W)
+        lat.sync()
+        barrier()
+        l0 = lat.observables()["kernel_launches"]
+        if timing:
+            lat.set_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            lat.sweep(K)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        ph = lat.timing() if timing else None
+        if timing:
+            lat.set_timing(False)
+        launches = lat.observables()["kernel_launches"] - l0
+        return ms, ph, launches
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    out = {}
+    lat = lattice(sco.FP64)
+    with ClockSampler(local) as clk:
+        ms, ph, launches = timed(lat, args.steps, args.warmup, timing=True)
+    ms = max_over_ranks(ms)
+    obs = lat.observables()
+    out["fp64"] = dict(ms=ms, phases=ph, launches=launches, obs=obs, clocks=clk.summary())
+    if not args.no_e2e:
+        # end to end through the public API with host buffers: every step copies the spins
+        # in from pinned host memory and the spins out to pinned host memory
+        hin = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+        hout = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+        import ctypes as C
+        Lb = sco.load()
+        st = Lb.sco_get_spins(lat.handle, C.c_void_p(hin.data_ptr()), 0)
+        assert st == 0
+        K = max(1, args.steps // 2)
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            assert Lb.sco_set_spins(lat.handle, C.c_void_p(hin.data_ptr()), 0) == 0
+            lat.sweep(1)
+            assert Lb.sco_get_spins(lat.handle, C.c_void_p(hout.data_ptr()), 0) == 0
+            hin, hout = hout, hin
+        torch.cuda.synchronize(dev)
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        out["e2e"] = dict(value=N * K * world / t_e2e, unit=UNIT, h2d_bytes_per_step=3 * N * 8,
+                          d2h_bytes_per_step=3 * N * 8, steps=K)
+    lat.close()
+    del lat
+    if not args.no_fp32:
+        lat32 = lattice(sco.FP32_GUARDED)
+        ms32, ph32, l32 = timed(lat32, args.steps, args.warmup, timing=True)
+        ms32 = max_over_ranks(ms32)
+        out["fp32"] = dict(ms=ms32, phases=ph32, launches=l32, obs=lat32.observables())
+        lat32.close()
+    return out
+
+
+def cpu_baseline(L, T, seed):
+    import oracle as O
+
+    ncores = os.cpu_count() or 1
+    O.set_threads(ncores)
+    ch = O.Chain(O.make_params(L, T=T, seed=seed))
+    t0 = time.perf_counter()
+    ch.sweep(1)
+    dt = time.perf_counter() - t0
+    return {"value": L * L / dt, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": "1 MC step (switch+colour+sweep, n_sw=1) of the L=%d lattice at T=%gD "
+                      "from the seed-%d start, %d OpenMP threads, %.1f s" % (L, T, seed, ncores, dt)}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world, local)
+    if rank != 0:
+        return
+    N = args.L * args.L
+    K = args.steps
+    f64 = res["fp64"]
+    value = N * K * world / (f64["ms"] / 1e3)
+    obs = f64["obs"]
+    k = 2.0 * obs["n_edges"] / N
+    levels = 0
+    g = obs["max_degree"] + 1
+    G = -(-N // g)
+    while (1 << levels) < G:
+        levels += 1
+    ab = algorithmic_bytes(k, levels)
+    ph = f64["phases"]
+    per_step = {"switch": ph["switch_ms"] / max(ph["switch_calls"], 1),
+                "colour": ph["colour_ms"] / max(ph["colour_calls"], 1),
+                "sweep": ph["sweep_ms"] / max(ph["sweep_calls"], 1)}
+    dom = max(per_step, key=per_step.get)
+    hbm, how = peaks()
+    achieved = ab[dom] * N / (per_step[dom] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": f64["ms"] / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "L=%d open lattice, J=0, D=1, T=%gD, seed %d, n_sw=1, FP64" % (
+            args.L, args.T, args.seed), "L": args.L, "N": N, "T": args.T,
+            "precision": "fp64", "parallelism": "replicas" if world > 1 else "single",
+            "l2": "working set > L2 (spins %.0f MB + CSR %.0f MB + tables)" % (
+                3 * N * 8 / 1e6, 2 * obs["n_edges"] * 4 / 1e6)},
+        "gpu_launches": f64["launches"],
+        "clocks": f64["clocks"],
+        "phases_ms_per_step": per_step,
+        "graph": {"mean_degree": k, "max_degree": obs["max_degree"],
+                  "n_colours": obs["n_colours"], "kw_rounds": obs["kw_rounds"],
+                  "kw_levels": levels},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_source": how, "algorithmic_bytes_per_update": ab[dom]},
+    }
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+    if "fp32" in res:
+        f32 = res["fp32"]
+        p32 = f32["phases"]
+        line["fp32_guarded"] = {
+            "value": N * K * world / (f32["ms"] / 1e3), "ms_per_step": f32["ms"] / K,
+            "gpu_launches": f32["launches"],
+            "phases_ms_per_step": {
+                "switch": p32["switch_ms"] / max(p32["switch_calls"], 1),
+                "colour": p32["colour_ms"] / max(p32["colour_calls"], 1),
+                "sweep": p32["sweep_ms"] / max(p32["sweep_calls"], 1)},
+            "guard_hits_fp32": f32["obs"]["guard_hits_fp32"],
+            "guard_hits_fp64": f32["obs"]["guard_hits_fp64"]}
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_L, args.T, args.seed)
+    print(json.dumps(line), flush=True)
+
+
+def reference_arm(args, rank, world):
+    """The oracle (plain C, all host cores) timed on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle as O
+
+    ncores = os.cpu_count() or 1
+    O.set_threads(ncores)
+    L = args.ref_L
+    ch = O.Chain(O.make_params(L, T=args.T, seed=args.seed))
+    ch.sweep(args.warmup)
+    t0 = time.perf_counter()
+    ch.sweep(args.steps)
+    dt = time.perf_counter() - t0
+    value = L * L * args.steps / dt
+    sample = ("%d MC steps (switch+colour+sweep, n_sw=1) of an L=%d lattice at T=%gD, %d OpenMP "
+              "threads, %.1f s; per-site work matches the L=%d workload" % (
+                  args.steps, L, args.T, ncores, dt, args.L))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": "L=%d open lattice, J=0, D=1, T=%gD, seed %d, n_sw=1, FP64" % (
+            args.L, args.T, args.seed), "L": args.L, "N": args.L * args.L, "T": args.T,
+            "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,156 @@
+/*
+ * sco.h -- C ABI of the GB300 library for the per-sweep hot path of the parallelized
+ * stochastic cutoff (SCO) method of Endo, Toga and Sasaki (arXiv:1503.03295).
+ *
+ * One lattice (or a batch of replicas) lives in an opaque context that owns every device
+ * buffer.  All work is enqueued on the CUDA stream given at creation; calls return a
+ * status and never abort.  Every step of the path runs in the library's own CUDA kernels
+ * (compute capability 10.3, sm_103a); there is no CPU fallback: without a usable device
+ * sco_init returns SCO_ECUDA.
+ *
+ * Model (Sec. 3.1, Eq. (6)): open Lx x Ly square lattice, site i = x + Lx*y at r_i = (x, y),
+ * classical Heisenberg spins |S| = 1,
+ *     H = -J sum_<ij> S_i.S_j + D sum_{i<j} [S_i.S_j / r^3 - 3 (S_i.r)(S_j.r) / r^5].
+ * The SCO switching (Sec. 2.1, Eqs. (1)-(3)) acts on the dipolar term; nearest-neighbour
+ * exchange bonds are always present and join the colouring graph when J != 0.
+ *
+ * Per MC step (Fig. 1): (1) switch every dipolar pair to 0 or to its pseudointeraction,
+ * (2) colour the graph of surviving pairs (Kuhn-Wattenhofer, Sec. 2.3), (3) update all
+ * sites of each colour at once (Metropolis, uniform new direction).  Random numbers come
+ * from Philox4x64-10 keyed by (seed, replica) with counter (site, step or epoch, draw,
+ * tag), so a trajectory is a pure function of the parameters.
+ *
+ * Layouts: spins are SoA, three arrays of N doubles (x then y then z).  Graph: CSR with
+ * row_ptr (N + 1 uint32) and col (uint32); rows sorted by neighbour index; bit 31 of a col
+ * entry marks an exchange bond whose dipolar pair was switched to zero.
+ *
+ * Errors: SCO_EINVAL for bad arguments (nothing changed); SCO_ECUDA when a CUDA call fails
+ * (the context should be destroyed); SCO_ETIMEOUT / SCO_ECAPACITY are raised on the device
+ * (bounded waits, fixed-size buffers), become sticky, and are returned by the next call
+ * that synchronises (sco_sync, sco_colour with a non-NULL count, getters, observables).
+ */
+#ifndef SCO_H
+#define SCO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SCO_OK = 0,
+  SCO_EINVAL = 1,     /* invalid argument or size */
+  SCO_ENOMEM = 2,     /* device allocation failed */
+  SCO_ECUDA = 3,      /* a CUDA runtime call failed (or no device) */
+  SCO_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+  SCO_ESTATE = 5,     /* call not valid in the current state (e.g. bad checkpoint) */
+  SCO_EGUARD = 6,     /* reserved */
+  SCO_ECAPACITY = 7   /* a fixed-size device buffer overflowed */
+} sco_status;
+
+typedef enum { SCO_FP64 = 0, SCO_FP32_GUARDED = 1 } sco_precision;
+
+typedef struct {
+  int32_t Lx, Ly;         /* lattice, 1 <= Lx, Ly <= 32767, Lx*Ly < 2^30 */
+  double J;               /* exchange constant */
+  double D;               /* dipolar constant, >= 0 */
+  double T;               /* temperature > 0; beta = fl(1/T) */
+  uint64_t seed;          /* Philox key word 0 */
+  int32_t n_sw;           /* switch + colour every n_sw MC steps (Sec. 2.1 step (B)), >= 1 */
+  int32_t precision;      /* sco_precision */
+  int32_t colour_variant; /* 0: KW over modified BCR (2)'; 1: KW over plain BCR (2) */
+  int32_t replica;        /* Philox key word 1 */
+} sco_params;
+
+typedef struct {
+  double e_switched; /* H' of Eq. (4) (pseudointeractions of surviving pairs) + exchange */
+  double e_exchange; /* -J sum_<ij> S_i.S_j */
+  double e_full;     /* full H of Eq. (6) by direct summation; NaN unless requested */
+  double mx, my, mz; /* magnetisation per spin */
+  double m_abs;      /* |m| */
+  double m_phi;      /* signed [(1/N) sum S_i x (r_i - r_c)/|r_i - r_c|]_z of Eq. (7) */
+  int64_t n_edges;   /* surviving dipolar pairs */
+  int32_t max_degree;         /* Delta of the colouring graph */
+  int32_t n_colours;          /* non-empty colour classes */
+  int32_t kw_rounds;          /* running time t_R of the colouring (Sec. 2.3.1, Eq. (5)) */
+  int32_t max_degree_dipolar; /* Delta over dipolar pairs only (as in Table 1) */
+  int64_t sweeps_done;        /* MC steps done */
+  int64_t guard_hits_fp64;    /* decisions re-evaluated in double-double */
+  int64_t guard_hits_fp32;    /* FP32 decisions re-evaluated in FP64 */
+  int64_t kernel_launches;    /* kernels launched by this context so far */
+} sco_obs;
+
+typedef struct sco_ctx sco_ctx;
+
+/* Creates a lattice: builds the coupling table, allocates every buffer and draws the
+ * initial spins (uniform on the sphere, Philox tag INIT).  stream: a cudaStream_t (NULL =
+ * legacy default stream); the caller keeps it alive until sco_destroy.  On success *out
+ * owns all device memory.  Synchronises once. */
+sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out);
+void sco_destroy(sco_ctx* c);
+
+/* Step (A), Sec. 2.1: switches every dipolar pair at epoch t / n_sw from the current spins
+ * (Eqs. (1)-(2)) and compacts the survivors into the CSR graph.  Synchronises once (to
+ * size the graph). */
+sco_status sco_switch(sco_ctx* c);
+
+/* Step (2) of Fig. 1, Sec. 2.3.3: Kuhn-Wattenhofer (Delta+1)-colouring of the current graph
+ * and the colour classes.  Switches first if no graph exists.  n_colours may be NULL. */
+sco_status sco_colour(sco_ctx* c, int32_t* n_colours);
+
+/* Steps (B)-(C), Sec. 2.1: n_mcs MC steps; before step t, if the graph is not the one of
+ * epoch t / n_sw, switch and colour again.  One MC step updates every site once. */
+sco_status sco_sweep(sco_ctx* c, int32_t n_mcs);
+
+/* Observables of the current state (Eqs. (4), (6), (7), Table 1).  want_full computes the
+ * full H by O(N^2) direct summation (N <= 65536, else e_full = NaN).  Synchronises. */
+sco_status sco_observables(sco_ctx* c, sco_obs* out, int32_t want_full);
+
+/* Spin copies (SoA, 3*N doubles).  on_device != 0: xyz is a device pointer.  Synchronous. */
+sco_status sco_get_spins(sco_ctx* c, double* xyz, int32_t on_device);
+sco_status sco_set_spins(sco_ctx* c, const double* xyz, int32_t on_device);
+
+/* Sizes: sites, CSR entries of the current graph (0 if none), max degree, colour count
+ * (Delta + 1 palette size).  Any pointer may be NULL. */
+sco_status sco_get_sizes(sco_ctx* c, int64_t* n_sites, int64_t* n_entries, int32_t* max_degree,
+                         int32_t* palette);
+
+/* Host copies of the graph: row_ptr (N + 1), col (n_entries), colour (N); NULL skips. */
+sco_status sco_get_graph(sco_ctx* c, uint32_t* row_ptr, uint32_t* col, uint32_t* colour);
+
+/* Host copies of the colour classes: perm (N sites grouped by colour; order inside a class
+ * unspecified) and off (palette + 1 offsets). */
+sco_status sco_get_classes(sco_ctx* c, uint32_t* perm, uint32_t* off);
+
+/* Accept bit per site of the last MC step (N bytes, host). */
+sco_status sco_get_accepts(sco_ctx* c, uint8_t* acc);
+
+/* Host copy of the sorted half-plane coupling table: dx, dy (K int32 each), hazard prefix
+ * W (K uint64) and c(r^2) ~ r^-5 (K doubles); K = (Lx-1) + (Ly-1)(2Lx-1). */
+sco_status sco_get_table(sco_ctx* c, int64_t* K, int32_t* dx, int32_t* dy, uint64_t* W,
+                         double* cc);
+
+/* Checkpoint: a byte blob holding the parameters, the step counter, the spins and (when the
+ * current epoch started before the current step) the spins at the epoch start, from which
+ * the epoch's graph is rebuilt.  sco_get_state with buf == NULL returns the size in *len.
+ * Restoring then continuing is bit-identical to an uninterrupted run. */
+sco_status sco_get_state(sco_ctx* c, void* buf, size_t* len);
+sco_status sco_set_state(sco_ctx* c, const void* buf, size_t len);
+
+/* Device time (ms) spent in each phase since the last reset, measured with CUDA events on
+ * the context's stream when enabled: [0] switch + CSR, [1] colouring + classes,
+ * [2] colour-class sweeps.  enable = 0 stops recording. */
+sco_status sco_set_timing(sco_ctx* c, int32_t enable);
+sco_status sco_get_timing(sco_ctx* c, double ms[3], int64_t calls[3]);
+
+/* Waits for the context's stream; returns the sticky device status. */
+sco_status sco_sync(sco_ctx* c);
+
+const char* sco_strerror(sco_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

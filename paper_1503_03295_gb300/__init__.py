@@ -1,0 +1,245 @@
+"""GB300 library for the per-sweep hot path of the parallelized stochastic cutoff (SCO)
+method (Endo, Toga and Sasaki, arXiv:1503.03295).
+
+This module only marshals arguments to the C ABI of ``lib/libsco.so`` (declared in
+``include/sco.h``); every step of the path runs in the library's CUDA kernels.  There is
+no fallback: importing works anywhere, but creating a :class:`Lattice` without a usable
+CUDA device, or without the built library, raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libsco.so")
+
+SCO_OK, SCO_EINVAL, SCO_ENOMEM, SCO_ECUDA, SCO_ETIMEOUT, SCO_ESTATE, SCO_EGUARD, SCO_ECAPACITY = range(8)
+FP64, FP32_GUARDED = 0, 1
+EXCH_ONLY = 0x80000000
+
+
+class ScoError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, strerror(status), status))
+
+
+class Params(C.Structure):
+    _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32), ("J", C.c_double), ("D", C.c_double),
+                ("T", C.c_double), ("seed", C.c_uint64), ("n_sw", C.c_int32),
+                ("precision", C.c_int32), ("colour_variant", C.c_int32), ("replica", C.c_int32)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("e_switched", C.c_double), ("e_exchange", C.c_double), ("e_full", C.c_double),
+                ("mx", C.c_double), ("my", C.c_double), ("mz", C.c_double),
+                ("m_abs", C.c_double), ("m_phi", C.c_double), ("n_edges", C.c_int64),
+                ("max_degree", C.c_int32), ("n_colours", C.c_int32), ("kw_rounds", C.c_int32),
+                ("max_degree_dipolar", C.c_int32), ("sweeps_done", C.c_int64),
+                ("guard_hits_fp64", C.c_int64), ("guard_hits_fp32", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load():
+    """Load lib/libsco.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsco.so is not built; run paper_1503_03295_gb300._build.build() "
+                           "or __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, st = C.c_void_p, C.c_int
+    sig = {
+        "sco_init": ([C.POINTER(Params), vp, C.POINTER(vp)], st),
+        "sco_destroy": ([vp], None),
+        "sco_switch": ([vp], st),
+        "sco_colour": ([vp, C.POINTER(C.c_int32)], st),
+        "sco_sweep": ([vp, C.c_int32], st),
+        "sco_observables": ([vp, C.POINTER(Obs), C.c_int32], st),
+        "sco_get_spins": ([vp, vp, C.c_int32], st),
+        "sco_set_spins": ([vp, vp, C.c_int32], st),
+        "sco_get_sizes": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                           C.POINTER(C.c_int32)], st),
+        "sco_get_graph": ([vp, vp, vp, vp], st),
+        "sco_get_classes": ([vp, vp, vp], st),
+        "sco_get_accepts": ([vp, vp], st),
+        "sco_get_table": ([vp, C.POINTER(C.c_int64), vp, vp, vp, vp], st),
+        "sco_get_state": ([vp, vp, C.POINTER(C.c_size_t)], st),
+        "sco_set_state": ([vp, vp, C.c_size_t], st),
+        "sco_set_timing": ([vp, C.c_int32], st),
+        "sco_get_timing": ([vp, vp, vp], st),
+        "sco_sync": ([vp], st),
+        "sco_strerror": ([C.c_int], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def strerror(status):
+    try:
+        return load().sco_strerror(int(status)).decode()
+    except Exception:
+        return "status %d" % status
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _check(status, what):
+    if status != SCO_OK:
+        raise ScoError(status, what)
+
+
+def make_params(Lx, Ly=None, T=1.0, D=1.0, J=0.0, seed=0, n_sw=1, precision=FP64,
+                colour_variant=0, replica=0):
+    return Params(Lx, Lx if Ly is None else Ly, J, D, T, seed, n_sw, precision, colour_variant,
+                  replica)
+
+
+class Lattice:
+    """One SCO lattice on the GPU (a thin handle on ``sco_ctx``).
+
+    ``stream`` is a CUDA stream handle (int) or None for the legacy default stream, e.g.
+    ``torch.cuda.current_stream().cuda_stream``.
+    """
+
+    def __init__(self, params=None, stream=None, **kw):
+        self.params = params if params is not None else make_params(**kw)
+        L = load()
+        h = C.c_void_p()
+        _check(L.sco_init(C.byref(self.params), C.c_void_p(stream or 0), C.byref(h)), "sco_init")
+        self._h = h
+        self.N = self.params.Lx * self.params.Ly
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sco_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---- the path -------------------------------------------------------------------
+    def switch(self):
+        _check(load().sco_switch(self._h), "sco_switch")
+
+    def colour(self, count=True):
+        n = C.c_int32(0)
+        _check(load().sco_colour(self._h, C.byref(n) if count else None), "sco_colour")
+        return n.value if count else None
+
+    def sweep(self, n=1):
+        _check(load().sco_sweep(self._h, int(n)), "sco_sweep")
+
+    def observables(self, full=False):
+        o = Obs()
+        _check(load().sco_observables(self._h, C.byref(o), int(bool(full))), "sco_observables")
+        return o.as_dict()
+
+    def sync(self):
+        _check(load().sco_sync(self._h), "sco_sync")
+
+    # ---- data -----------------------------------------------------------------------
+    def spins(self):
+        a = np.empty(3 * self.N)
+        _check(load().sco_get_spins(self._h, _ptr(a), 0), "sco_get_spins")
+        return a
+
+    def set_spins(self, xyz):
+        a = np.ascontiguousarray(xyz, np.float64)
+        if a.size != 3 * self.N:
+            raise ValueError("expected %d values" % (3 * self.N))
+        _check(load().sco_set_spins(self._h, _ptr(a), 0), "sco_set_spins")
+
+    def get_spins_device(self, dev_ptr):
+        _check(load().sco_get_spins(self._h, C.c_void_p(dev_ptr), 1), "sco_get_spins")
+
+    def set_spins_device(self, dev_ptr):
+        _check(load().sco_set_spins(self._h, C.c_void_p(dev_ptr), 1), "sco_set_spins")
+
+    def sizes(self):
+        n, e, d, g = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
+        _check(load().sco_get_sizes(self._h, C.byref(n), C.byref(e), C.byref(d), C.byref(g)),
+               "sco_get_sizes")
+        return n.value, e.value, d.value, g.value
+
+    def graph(self):
+        _, nnz, _, _ = self.sizes()
+        rp = np.empty(self.N + 1, np.uint32)
+        col = np.empty(max(nnz, 1), np.uint32)
+        _check(load().sco_get_graph(self._h, _ptr(rp), _ptr(col), None), "sco_get_graph")
+        return rp, col[:nnz]
+
+    def colours(self):
+        c = np.empty(self.N, np.uint32)
+        _check(load().sco_get_graph(self._h, None, None, _ptr(c)), "sco_get_graph")
+        return c
+
+    def classes(self):
+        _, _, _, g = self.sizes()
+        perm = np.empty(self.N, np.uint32)
+        off = np.empty(g + 1, np.uint32)
+        _check(load().sco_get_classes(self._h, _ptr(perm), _ptr(off)), "sco_get_classes")
+        return perm, off
+
+    def accepts(self):
+        a = np.empty(self.N, np.uint8)
+        _check(load().sco_get_accepts(self._h, _ptr(a)), "sco_get_accepts")
+        return a
+
+    def table(self):
+        K = C.c_int64()
+        _check(load().sco_get_table(self._h, C.byref(K), None, None, None, None), "sco_get_table")
+        k = K.value
+        dx, dy = np.empty(k, np.int32), np.empty(k, np.int32)
+        W, cc = np.empty(k, np.uint64), np.empty(k)
+        _check(load().sco_get_table(self._h, C.byref(K), _ptr(dx), _ptr(dy), _ptr(W), _ptr(cc)),
+               "sco_get_table")
+        return dict(dx=dx, dy=dy, W=W, Dc=cc)
+
+    def get_state(self):
+        n = C.c_size_t(0)
+        _check(load().sco_get_state(self._h, None, C.byref(n)), "sco_get_state")
+        buf = np.empty(n.value, np.uint8)
+        _check(load().sco_get_state(self._h, _ptr(buf), C.byref(n)), "sco_get_state")
+        return buf.tobytes()
+
+    def set_state(self, blob):
+        buf = np.frombuffer(blob, np.uint8).copy()
+        _check(load().sco_set_state(self._h, _ptr(buf), buf.size), "sco_set_state")
+
+    def set_timing(self, enable=True):
+        _check(load().sco_set_timing(self._h, int(bool(enable))), "sco_set_timing")
+
+    def timing(self):
+        ms = np.zeros(3)
+        calls = np.zeros(3, np.int64)
+        _check(load().sco_get_timing(self._h, _ptr(ms), _ptr(calls)), "sco_get_timing")
+        return dict(switch_ms=ms[0], colour_ms=ms[1], sweep_ms=ms[2], switch_calls=int(calls[0]),
+                    colour_calls=int(calls[1]), sweep_calls=int(calls[2]))

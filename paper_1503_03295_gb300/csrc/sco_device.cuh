@@ -1,0 +1,234 @@
+// sco_device.cuh -- device-side building blocks of the SCO library (sm_103a):
+// counter-based random numbers, the spin proposal, the dipolar pair energy,
+// double-double arithmetic for near-tie decisions, and the kernel parameter block.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sco {
+
+// Philox counter word 3 per use of the random stream (the library's stream layout).
+constexpr uint64_t kTagInit = 1, kTagSwitch = 2, kTagPropose = 3;
+// Bit 31 of a CSR entry: nearest-neighbour exchange bond whose dipolar pair was switched off.
+constexpr uint32_t kExchOnly = 0x80000000u;
+constexpr uint32_t kIndexMask = 0x7FFFFFFFu;
+
+// Parameters every kernel reads (passed by value).
+struct DevParams {
+  int32_t Lx, Ly;
+  int64_t N;        // Lx * Ly
+  int64_t K;        // half-plane displacement count
+  double J, D, beta, bD;  // beta = fl(1/T), bD = fl(beta * D)
+  uint64_t key0, key1;    // Philox key: seed, replica
+  double ln2_hi, ln2_lo;  // ln 2 as a double-double
+};
+
+// ---------------------------------------------------------------------------------------
+// Philox4x64-10, Salmon, Moraes, Dror and Shaw (SC'11): two 64x64->128 multiplies per round
+// on counter words 0 and 2, high halves mixed with words 1, 3 and the key, key bumped by
+// the Weyl increments after every round.
+struct W4 {
+  uint64_t w[4];
+};
+
+__device__ __forceinline__ W4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                     uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t B0 = 0x9E3779B97F4A7C15ull, B1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += B0;
+    k1 += B1;
+  }
+  W4 o;
+  o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+  return o;
+}
+
+__device__ __forceinline__ double u53(uint64_t w) { return (double)(w >> 11) * 0x1p-53; }
+__device__ __forceinline__ double u53pos(uint64_t w) {
+  return ((double)(w >> 11) + 1.0) * 0x1p-53;
+}
+
+// Marsaglia (1972): reject unless 0 < s = a1^2 + a2^2 < 1, then
+// S = (2 a1 sqrt(1-s), 2 a2 sqrt(1-s), 1 - 2s).  Each operation rounded on its own so that
+// the spin is the same bit pattern on every IEEE machine.
+__device__ __forceinline__ bool marsaglia(uint64_t w0, uint64_t w1, double& x, double& y,
+                                          double& z) {
+  const double a1 = __dsub_rn(__dmul_rn(2.0, u53(w0)), 1.0);
+  const double a2 = __dsub_rn(__dmul_rn(2.0, u53(w1)), 1.0);
+  const double s = __dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2));
+  if (s >= 1.0 || s == 0.0) return false;
+  const double h = __dsqrt_rn(__dsub_rn(1.0, s));
+  x = __dmul_rn(__dmul_rn(2.0, a1), h);
+  y = __dmul_rn(__dmul_rn(2.0, a2), h);
+  z = __dsub_rn(1.0, __dmul_rn(2.0, s));
+  return true;
+}
+
+// c(r^2) = fl(1 / fl(fl(r2 r2) fl(sqrt r2))): the FP64 constant standing for r^-5.
+__device__ __forceinline__ double coupling_c(int64_t r2) {
+  const double q = (double)r2;
+  return __ddiv_rn(1.0, __dmul_rn(__dmul_rn(q, q), __dsqrt_rn(q)));
+}
+
+// A(r^2) = trunc(fl(fl(2^60 / fl(r2 sqrt r2)) (1 + 2^-50))) + 1 > 2^60 / r^3, so that
+// V_max = D A 2^-59 >= 2D / r^3, the maximum of the dipolar pair energy.
+__device__ __forceinline__ uint64_t hazard_A(int64_t r2) {
+  const double q = (double)r2;
+  const double t = __ddiv_rn(0x1p60, __dmul_rn(q, __dsqrt_rn(q)));
+  return __double2ull_rz(__dmul_rn(t, 1.0 + 0x1p-50)) + 1ull;
+}
+
+// Dipolar pair energy of Eq. (6) with c ~ r^-5 and d = (dx, dy, 0):
+// V = D c [r^2 (S_i.S_j) - 3 (S_i.d)(S_j.d)].  |error| <= 2^-47 |D| c r^2 with or without FMA.
+__device__ __forceinline__ double pair_V(double Dc, double r2, double ax, double ay, double az,
+                                         double bx, double by, double bz, double fx, double fy) {
+  const double ss = ax * bx + ay * by + az * bz;
+  const double pa = ax * fx + ay * fy;
+  const double pb = bx * fx + by * fy;
+  return Dc * (r2 * ss - 3.0 * (pa * pb));
+}
+
+// ---------------------------------------------------------------------------------------
+// Double-double arithmetic (Dekker 1971; Knuth's two-sum; Hida, Li and Bailey's QD layout)
+// for re-evaluating decisions whose FP64 margin is inside its error bound.
+struct dd {
+  double hi, lo;
+};
+
+__host__ __device__ __forceinline__ dd two_sum(double a, double b) {
+  const double s = a + b;
+  const double bb = s - a;
+  const double e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__host__ __device__ __forceinline__ dd quick_two_sum(double a, double b) {
+  const double s = a + b;
+  return {s, b - (s - a)};
+}
+__host__ __device__ __forceinline__ dd two_prod(double a, double b) {
+  const double p = a * b;
+#ifdef __CUDA_ARCH__
+  return {p, __fma_rn(a, b, -p)};
+#else
+  return {p, __builtin_fma(a, b, -p)};
+#endif
+}
+__host__ __device__ __forceinline__ dd dd_from(double a) { return {a, 0.0}; }
+__host__ __device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  dd t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return quick_two_sum(s.hi, s.lo);
+}
+__host__ __device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+__host__ __device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+__host__ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  dd p = two_prod(a.hi, b.hi);
+  p.lo += a.hi * b.lo + a.lo * b.hi;
+  return quick_two_sum(p.hi, p.lo);
+}
+__host__ __device__ __forceinline__ dd dd_mul_d(dd a, double b) {
+  dd p = two_prod(a.hi, b);
+  p.lo += a.lo * b;
+  return quick_two_sum(p.hi, p.lo);
+}
+__host__ __device__ __forceinline__ dd dd_div(dd a, dd b) {
+  const double q1 = a.hi / b.hi;
+  dd r = dd_sub(a, dd_mul_d(b, q1));
+  const double q2 = r.hi / b.hi;
+  r = dd_sub(r, dd_mul_d(b, q2));
+  const double q3 = r.hi / b.hi;
+  dd q = quick_two_sum(q1, q2);
+  return dd_add(q, dd_from(q3));
+}
+__host__ __device__ __forceinline__ dd dd_ldexp(dd a, int e) {
+#ifdef __CUDA_ARCH__
+  return {scalbn(a.hi, e), scalbn(a.lo, e)};
+#else
+  return {__builtin_scalbn(a.hi, e), __builtin_scalbn(a.lo, e)};
+#endif
+}
+__host__ __device__ __forceinline__ bool dd_lt(dd a, dd b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__host__ __device__ __forceinline__ dd dd_from_u64(uint64_t a) {
+  const double hi = (double)(a & ~0x7FFull);  // top bits, exact
+  const double lo = (double)(a & 0x7FFull);   // low 11 bits, exact
+  return quick_two_sum(hi, lo);
+}
+
+// expm1 of a double-double of modulus < 1: x / 2^10, Taylor series, then ten doublings
+// t <- 2t + t^2 of e^y - 1 (keeps the relative accuracy near 0).
+__host__ __device__ inline dd dd_expm1_small(dd x) {
+  const dd y = dd_ldexp(x, -10);
+  dd term = y, sum = y;
+  for (int n = 2; n <= 14; ++n) {
+    term = dd_mul(term, y);
+    term = dd_div(term, dd_from((double)n));
+    sum = dd_add(sum, term);
+  }
+  for (int k = 0; k < 10; ++k) sum = dd_add(dd_ldexp(sum, 1), dd_mul(sum, sum));
+  return sum;
+}
+
+// exp and expm1 for a double-double: x = k ln2 + r, |r| <= ln2 / 2.
+__host__ __device__ inline dd dd_expm1(dd x, dd ln2) {
+  if (x.hi > 745.0) return {INFINITY, 0.0};
+  if (x.hi < -745.0) return {-1.0, 0.0};
+  const double kf = floor(x.hi / ln2.hi + 0.5);
+  const int k = (int)kf;
+  const dd r = dd_sub(x, dd_mul_d(ln2, kf));
+  const dd t = dd_expm1_small(r);
+  if (k == 0) return t;
+  // 2^k (1 + t) - 1
+  return dd_sub(dd_ldexp(dd_add(dd_from(1.0), t), k), dd_from(1.0));
+}
+__host__ __device__ inline dd dd_exp(dd x, dd ln2) {
+  return dd_add(dd_expm1(x, ln2), dd_from(1.0));
+}
+// log by one Newton step on exp from the FP64 logarithm: x1 = x0 + y e^-x0 - 1.
+__host__ __device__ inline dd dd_log(dd y, dd ln2) {
+#ifdef __CUDA_ARCH__
+  const double x0 = log(y.hi);
+#else
+  const double x0 = __builtin_log(y.hi);
+#endif
+  const dd e = dd_exp(dd_from(-x0), ln2);
+  const dd c = dd_sub(dd_mul(y, e), dd_from(1.0));
+  return dd_add(dd_from(x0), c);
+}
+// log(1 - e^x) for x < 0 (Maechler 2012 branch point at -ln 2).
+__host__ __device__ inline dd dd_log1mexp(dd x, dd ln2) {
+  if (x.hi > -ln2.hi) return dd_log(dd_neg(dd_expm1(x, ln2)), ln2);
+  return dd_log(dd_sub(dd_from(1.0), dd_exp(x, ln2)), ln2);
+}
+
+// V = D c [r^2 (a.b) - 3 (a.d)(b.d)] in double-double from FP64 inputs.
+__host__ __device__ inline dd dd_pair_V(double D, double c, double r2, const double* a,
+                                        const double* b, double fx, double fy) {
+  dd ss = two_prod(a[0], b[0]);
+  ss = dd_add(ss, two_prod(a[1], b[1]));
+  ss = dd_add(ss, two_prod(a[2], b[2]));
+  const dd pa = dd_add(two_prod(a[0], fx), two_prod(a[1], fy));
+  const dd pb = dd_add(two_prod(b[0], fx), two_prod(b[1], fy));
+  const dd inner = dd_sub(dd_mul_d(ss, r2), dd_mul_d(dd_mul(pa, pb), 3.0));
+  return dd_mul(two_prod(D, c), inner);
+}
+
+// V_max = D A 2^-59 in double-double.
+__host__ __device__ inline dd dd_vmax(double D, uint64_t A) {
+  return dd_ldexp(dd_mul_d(dd_from_u64(A), D), -59);
+}
+
+}  // namespace sco

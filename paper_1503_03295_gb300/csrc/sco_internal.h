@@ -1,0 +1,107 @@
+// sco_internal.h -- host-side declarations shared by the CUDA translation units of the
+// SCO library: the launchers each .cu file exports to the C-ABI layer (api.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sco_device.cuh"
+
+namespace sco {
+
+// Device-resident counters of one lattice (one struct per replica).
+struct DevCounters {
+  unsigned long long n_half;        // surviving half-plane pairs incl. exchange-only bonds
+  unsigned long long n_dip;         // surviving dipolar pairs
+  unsigned long long ovf_n;         // half-edges beyond the per-site slots
+  unsigned long long nnz;           // CSR entries
+  unsigned long long guard_fp64;    // decisions re-evaluated in double-double
+  unsigned long long guard_fp32;    // decisions re-evaluated in FP64 (FP32-guarded form)
+  unsigned int max_degree;          // Delta of the colouring graph
+  unsigned int max_degree_dip;      // Delta over dipolar pairs
+  unsigned int g;                   // Delta + 1
+  unsigned int levels;              // KW levels M
+  unsigned int kw_rounds;           // t_R (sum over levels of the deepest dependency chain)
+  unsigned int n_colours;           // non-empty classes
+  int status;                       // sticky device error (sco_status value), 0 if none
+  int pad;
+  double acc[8];                    // observable accumulators
+  unsigned int lev_rounds[32];      // deepest dependency chain per KW level
+};
+
+// ---- scan.cu ----
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t scan_excl_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* tmp,
+                          uint64_t* total_dev, cudaStream_t s, int64_t* launches);
+cudaError_t scan_incl_u64(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* tmp,
+                          uint64_t* total_dev, cudaStream_t s, int64_t* launches);
+
+// ---- table.cu ----
+struct Table {
+  int64_t K = 0;
+  uint32_t* disp = nullptr;  // packed (dx & 0xFFFF) | (dy << 16), sorted by (r^2, dy, dx)
+  uint64_t* W = nullptr;     // inclusive prefix of the integer hazards A_m
+  double2* xy = nullptr;     // by (|dx|, |dy|): {fl(D c(r^2)), V_max = fl(fl(D A) 2^-59)}
+  float4* xy32 = nullptr;    // by (|dx|, |dy|): FP32 copies {Dc, Vmax, 2 beta Vmax, 0}
+  int32_t m_nn[2] = {-1, -1};
+};
+cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches);
+void table_free(Table& t);
+
+// ---- init / observables (spins.cu) ----
+cudaError_t spins_init(const DevParams& P, double* s, float* s32, cudaStream_t st,
+                       int64_t* launches);
+cudaError_t spins_to_f32(int64_t N, const double* s, float* s32, cudaStream_t st,
+                         int64_t* launches);
+cudaError_t observables_run(const DevParams& P, const double* s, const uint32_t* row_ptr,
+                            const uint32_t* col, const double2* xy, bool have_graph,
+                            bool want_full, DevCounters* cnt, cudaStream_t st, int64_t* launches);
+
+// ---- switch.cu ----
+constexpr int kSlotCap = 32;
+struct SwitchBufs {
+  uint32_t* hslot;  // N * kSlotCap upper neighbours (j | flag) per site
+  uint32_t* hcnt;   // N half-degree per site
+  uint32_t* indeg;  // N lower-neighbour count per site (also the fill cursor base)
+  uint32_t* deg;    // N + 1
+  uint32_t* lcur;   // N lower fill cursor
+  uint32_t* ocur;   // N overflow fill cursor
+  uint32_t* ovf;    // 2 * ovf_cap (i, j | flag)
+  uint32_t ovf_cap;
+  uint64_t* scan_tmp;
+};
+cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float* s32,
+                       int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,
+                       cudaStream_t st, int64_t* launches);
+cudaError_t csr_scan(const DevParams& P, SwitchBufs& b, uint32_t* row_ptr, DevCounters* cnt,
+                     cudaStream_t st, int64_t* launches);
+cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* row_ptr,
+                     uint32_t* col, bool has_overflow, DevCounters* cnt, cudaStream_t st,
+                     int64_t* launches);
+
+// ---- colour.cu ----
+struct ColourBufs {
+  unsigned long long* word;  // N packed (level tag, round, colour)
+  uint32_t* colour;  // N final colours
+  uint32_t* hist;    // g + 1
+  uint32_t* off;     // g + 1
+  uint32_t* cursor;  // g
+  uint32_t* perm;    // N
+  uint64_t* scan_tmp;
+};
+cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
+                   uint32_t g, int variant, ColourBufs& b, DevCounters* cnt, cudaStream_t st,
+                   int64_t* launches);
+cudaError_t bucket_run(const DevParams& P, uint32_t g, ColourBufs& b, DevCounters* cnt,
+                       cudaStream_t st, int64_t* launches);
+
+// ---- sweep.cu ----
+cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float* s32,
+                      const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,
+                      const uint32_t* off, uint32_t g, uint64_t step, int precision,
+                      uint8_t* acc, DevCounters* cnt, cudaStream_t st, int64_t* launches);
+
+int num_sms();
+
+}  // namespace sco

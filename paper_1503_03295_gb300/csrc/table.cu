@@ -1,0 +1,147 @@
+// table.cu -- the translation-invariant coupling table, built on the device.
+//
+// Every unordered pair of the open lattice is (i, i + d) for one d of the half plane
+// {dy > 0, |dx| < Lx} u {dy = 0, 0 < dx < Lx}.  The list is sorted by (r^2, dy, dx) with a
+// stable counting sort on r^2 (rows are placed in increasing dy, and inside a row the
+// negative dx before the positive one), each element carries the integer hazard
+// A(r^2) > 2^60 / r^3 of its pair (V_max = D A 2^-59 >= 2D / r^3, Sec. 2.1), and W is the
+// inclusive prefix of A.  A second table indexed by (|dx|, |dy|) holds fl(D c(r^2)) and
+// V_max for the pair-energy evaluations of the switch and sweep kernels.
+#include <cstdint>
+
+#include "sco_internal.h"
+
+namespace sco {
+
+namespace {
+
+__device__ __forceinline__ void disp_of_q(int64_t q, int32_t Lx, int32_t& dx, int32_t& dy) {
+  if (q < Lx - 1) {
+    dx = (int32_t)q + 1;
+    dy = 0;
+    return;
+  }
+  const int64_t r = q - (Lx - 1);
+  const int64_t w = 2 * (int64_t)Lx - 1;
+  dy = (int32_t)(r / w) + 1;
+  dx = (int32_t)(r % w) - (Lx - 1);
+}
+
+__global__ void k_r2_count(int32_t Lx, int64_t K, uint32_t* __restrict__ cnt) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= K) return;
+  int32_t dx, dy;
+  disp_of_q(q, Lx, dx, dy);
+  atomicAdd(&cnt[(int64_t)dx * dx + (int64_t)dy * dy], 1u);
+}
+
+// One block walks the rows dy = 0..Ly-1 in order.  Inside a row the values |dx| are
+// distinct, hence so are the r^2, so the threads of a row never touch the same bucket.
+__global__ void __launch_bounds__(1024) k_order(int32_t Lx, int32_t Ly,
+                                                const uint32_t* __restrict__ start,
+                                                uint32_t* __restrict__ seen,
+                                                uint32_t* __restrict__ disp) {
+  for (int32_t dy = 0; dy < Ly; ++dy) {
+    for (int32_t ax = threadIdx.x; ax < Lx; ax += blockDim.x) {
+      if (dy == 0 && ax == 0) continue;
+      const int64_t r2 = (int64_t)ax * ax + (int64_t)dy * dy;
+      uint32_t m = start[r2] + seen[r2];
+      uint32_t n = 0;
+      if (dy > 0 && ax > 0) {  // (-ax, dy) precedes (ax, dy)
+        disp[m++] = ((uint32_t)(uint16_t)(int16_t)(-ax)) | ((uint32_t)dy << 16);
+        ++n;
+      }
+      disp[m] = ((uint32_t)(uint16_t)(int16_t)ax) | ((uint32_t)dy << 16);
+      ++n;
+      seen[r2] += n;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_hazard(int64_t K, const uint32_t* __restrict__ disp, uint64_t* __restrict__ A) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= K) return;
+  const uint32_t d = disp[m];
+  const int32_t dx = (int16_t)(d & 0xFFFFu), dy = (int32_t)(d >> 16);
+  A[m] = hazard_A((int64_t)dx * dx + (int64_t)dy * dy);
+}
+
+__global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __restrict__ xy,
+                     float4* __restrict__ xy32) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= (int64_t)Lx * Ly) return;
+  const int64_t ax = q % Lx, ay = q / Lx;
+  const int64_t r2 = ax * ax + ay * ay;
+  double dc = 0.0, vm = 0.0;
+  if (r2 > 0) {
+    dc = __dmul_rn(D, coupling_c(r2));
+    vm = __dmul_rn(__dmul_rn(D, (double)hazard_A(r2)), 0x1p-59);
+  }
+  xy[q] = make_double2(dc, vm);
+  xy32[q] = make_float4((float)dc, (float)vm, (float)(2.0 * beta * vm), 0.f);
+}
+
+}  // namespace
+
+cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches) {
+  cudaError_t e;
+  t.K = P.K;
+  const int64_t nxy = (int64_t)P.Lx * P.Ly;
+  if ((e = cudaMalloc(&t.xy, nxy * sizeof(double2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&t.xy32, nxy * sizeof(float4))) != cudaSuccess) return e;
+  k_xy<<<(unsigned)((nxy + 255) / 256), 256, 0, s>>>(P.Lx, P.Ly, P.D, P.beta, t.xy, t.xy32);
+  ++*launches;
+  const int64_t K = P.K;
+  if ((e = cudaMalloc(&t.disp, (K > 0 ? K : 1) * sizeof(uint32_t))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&t.W, (K > 0 ? K : 1) * sizeof(uint64_t))) != cudaSuccess) return e;
+  if (K == 0) return cudaGetLastError();
+  const int64_t R2 = (int64_t)(P.Lx - 1) * (P.Lx - 1) + (int64_t)(P.Ly - 1) * (P.Ly - 1);
+  uint32_t *cnt = nullptr, *start = nullptr;
+  uint64_t *A = nullptr, *tmp = nullptr;
+  const int64_t ns = (R2 + 2 > K ? R2 + 2 : K);
+  e = cudaMalloc(&cnt, (R2 + 2) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&start, (R2 + 2) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&A, K * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&tmp, scan_tmp_bytes(ns));
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (R2 + 2) * sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    k_r2_count<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(P.Lx, K, cnt);
+    ++*launches;
+    e = scan_excl_u32(cnt, start, R2 + 1, tmp, nullptr, s, launches);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (R2 + 2) * sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    k_order<<<1, 1024, 0, s>>>(P.Lx, P.Ly, start, cnt, t.disp);
+    ++*launches;
+    k_hazard<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(K, t.disp, A);
+    ++*launches;
+    e = scan_incl_u64(A, t.W, K, tmp, nullptr, s, launches);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(cnt);
+  cudaFree(start);
+  cudaFree(A);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return e;
+  // table index of the two nearest-neighbour displacements (1,0) and (0,1)
+  uint32_t head[2] = {0, 0};
+  const int nh = K < 2 ? (int)K : 2;
+  if ((e = cudaMemcpy(head, t.disp, nh * sizeof(uint32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return e;
+  for (int q = 0; q < nh; ++q) {
+    if (head[q] == 1u) t.m_nn[0] = q;
+    if (head[q] == (1u << 16)) t.m_nn[1] = q;
+  }
+  return cudaGetLastError();
+}
+
+void table_free(Table& t) {
+  cudaFree(t.disp);
+  cudaFree(t.W);
+  cudaFree(t.xy);
+  cudaFree(t.xy32);
+  t = Table();
+}
+
+}  // namespace sco

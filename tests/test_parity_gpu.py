@@ -1,0 +1,183 @@
+"""Parity of the CUDA library (through the C ABI) with the oracle on the same seeded inputs.
+
+Integer and decision outputs must be bit-exact: coupling table, initial spins, CSR graph of
+surviving pairs, colours, t_R, colour classes (as sets), accept bits and spins after MC
+steps (spins depend only on random words and accept bits).  Energies: within 1e-12
+relative per spin (different summation order)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1503_03295_gb300 as sco
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-12
+
+
+def _pair(L, Ly=None, **kw):
+    prec = kw.pop("precision", sco.FP64)
+    g = sco.Lattice(sco.make_params(L, Ly, precision=prec, **kw))
+    o = O.Chain(O.make_params(L, Ly, **kw))
+    return g, o
+
+
+def _same_graph(g, o):
+    rg, cg = g.graph()
+    ro, co = o.graph()
+    assert np.array_equal(rg.astype(np.int64), ro)
+    assert np.array_equal(cg, co)
+
+
+def _same_energy(a, b, N):
+    assert abs(a - b) <= E_TOL * max(abs(a), abs(b), float(N))
+
+
+@pytest.mark.parametrize("Lx,Ly", [(16, 16), (33, 17), (1, 9), (7, 1), (64, 64)])
+def test_table_bit_exact(Lx, Ly):
+    g = sco.Lattice(sco.make_params(Lx, Ly, T=0.5))
+    t = g.table()
+    r = O.table(Lx, Ly)
+    assert np.array_equal(t["dx"], r["dx"]) and np.array_equal(t["dy"], r["dy"])
+    assert np.array_equal(t["W"], r["W"])
+    assert np.array_equal(t["Dc"], r["c"])  # D = 1: fl(D c) = c
+
+
+@pytest.mark.parametrize("seed", [0, 5, 2**40 + 3])
+def test_initial_spins_bit_exact(seed):
+    g, o = _pair(48, T=0.5, seed=seed)
+    assert np.array_equal(g.spins(), o.spins())
+
+
+@pytest.mark.parametrize("L,T,J,seed", [(16, 0.5, 0.0, 0), (64, 0.3, 0.0, 1), (64, 1.2, 0.0, 2),
+                                        (40, 0.6, 0.7, 3), (256, 0.6, 0.0, 1)])
+def test_switch_graph_bit_exact(L, T, J, seed):
+    g, o = _pair(L, T=T, J=J, seed=seed)
+    g.switch()
+    o.switch()
+    _same_graph(g, o)
+    og, oo = g.observables(), o.observables()
+    assert og["n_edges"] == oo["n_edges"]
+    assert og["max_degree"] == oo["max_degree"]
+    assert og["max_degree_dipolar"] == oo["max_degree_dipolar"]
+
+
+@pytest.mark.parametrize("L,T,variant", [(16, 0.5, 0), (64, 0.3, 0), (256, 0.6, 0), (64, 0.6, 1)])
+def test_colouring_bit_exact(L, T, variant):
+    g, o = _pair(L, T=T, seed=4, colour_variant=variant)
+    ng = g.colour()
+    no = o.colour()
+    assert ng == no
+    assert np.array_equal(g.colours().astype(np.int32), o.colours())
+    og, oo = g.observables(), o.observables()
+    assert og["kw_rounds"] == oo["kw_rounds"] and og["n_colours"] == oo["n_colours"]
+    perm_g, off_g = g.classes()
+    perm_o, off_o = o.classes()
+    assert np.array_equal(off_g.astype(np.int64), off_o[:len(off_g)])
+    for c in range(len(off_g) - 1):
+        a = np.sort(perm_g[off_g[c]:off_g[c + 1]]).astype(np.int64)
+        assert np.array_equal(a, perm_o[off_o[c]:off_o[c + 1]])
+
+
+@pytest.mark.parametrize("L,T,J,n", [(16, 0.5, 0.0, 200), (64, 0.3, 0.0, 20), (64, 1.2, 0.0, 20),
+                                     (32, 0.8, 1.0, 20)])
+def test_trajectory_bit_exact(L, T, J, n):
+    g, o = _pair(L, T=T, J=J, D=1.0 if J == 0 else 0.1, seed=7)
+    for k in range(n):
+        g.sweep(1)
+        o.sweep(1)
+        if k % max(1, n // 5) == 0 or k == n - 1:
+            assert np.array_equal(g.accepts(), o.accepts()), k
+            assert np.array_equal(g.spins(), o.spins()), k
+    _same_graph(g, o)
+    og, oo = g.observables(full=True), o.observables(full=True)
+    for key in ("e_switched", "e_exchange", "e_full"):
+        _same_energy(og[key], oo[key], g.N)
+    for key in ("mx", "my", "mz", "m_abs", "m_phi"):
+        assert abs(og[key] - oo[key]) < 1e-13
+    assert og["sweeps_done"] == oo["sweeps_done"] == n
+
+
+@pytest.mark.parametrize("T,seed", [(0.3, 1), (0.6, 2), (1.2, 3)])
+def test_l256_first_50_sweeps(T, seed):
+    g, o = _pair(256, T=T, seed=seed)
+    g.sweep(50)
+    o.sweep(50)
+    assert np.array_equal(g.spins(), o.spins())
+    _same_energy(g.observables()["e_switched"], o.observables()["e_switched"], g.N)
+
+
+@pytest.mark.parametrize("T", [0.4, 0.8])
+def test_fp32_guarded_matches_fp64_and_oracle(T):
+    L = 96
+    g64 = sco.Lattice(sco.make_params(L, T=T, seed=1))
+    g32 = sco.Lattice(sco.make_params(L, T=T, seed=1, precision=sco.FP32_GUARDED))
+    o = O.Chain(O.make_params(L, T=T, seed=1))
+    g64.sweep(15)
+    g32.sweep(15)
+    o.sweep(15)
+    s = o.spins()
+    assert np.array_equal(g64.spins(), s)
+    assert np.array_equal(g32.spins(), s)
+    e32, e64 = g32.observables(), g64.observables()
+    assert abs(e32["e_switched"] - e64["e_switched"]) <= 1e-6 * abs(e64["e_switched"])
+    assert e32["guard_hits_fp32"] > 0  # the FP32 screen did defer some decisions
+
+
+def test_edge_cases_tiny_lattices():
+    for (Lx, Ly) in [(1, 1), (2, 1), (1, 2), (3, 1)]:
+        g, o = _pair(Lx, Ly, T=0.3, seed=9)
+        g.sweep(5)
+        o.sweep(5)
+        assert np.array_equal(g.spins(), o.spins())
+        assert g.observables()["n_colours"] == o.observables()["n_colours"]
+
+
+def test_infinite_temperature_and_pure_exchange():
+    g, o = _pair(20, T=1e12, seed=2)
+    g.sweep(2)
+    o.sweep(2)
+    assert np.array_equal(g.spins(), o.spins()) and np.all(g.accepts() == 1)
+    assert g.observables()["n_edges"] == 0
+    g, o = _pair(12, T=0.7, J=1.0, D=0.0, seed=3)
+    g.sweep(4)
+    o.sweep(4)
+    assert np.array_equal(g.spins(), o.spins())
+    _same_graph(g, o)
+
+
+def test_checkpoint_resume_bit_exact():
+    for n_sw in (1, 3):
+        p = dict(T=0.5, seed=11, n_sw=n_sw)
+        a = sco.Lattice(sco.make_params(32, **p))
+        a.sweep(10)
+        ref = a.spins()
+        b = sco.Lattice(sco.make_params(32, **p))
+        b.sweep(4)
+        blob = b.get_state()
+        c = sco.Lattice(sco.make_params(32, **p))
+        c.set_state(blob)
+        c.sweep(6)
+        assert np.array_equal(c.spins(), ref)
+        o = O.Chain(O.make_params(32, **p))
+        o.sweep(10)
+        assert np.array_equal(o.spins(), ref)
+
+
+@pytest.mark.slow
+def test_full_size_first_sweep_L2304():
+    """The workload size of the throughput benchmark: L = 2304, T = 0.6 D, seed 0."""
+    g, o = _pair(2304, T=0.6, seed=0)
+    t = g.table()
+    r = O.table(2304)
+    idx = np.random.default_rng(0).integers(0, len(r["W"]), 200000)
+    assert np.array_equal(t["W"][idx], r["W"][idx]) and np.array_equal(t["dx"][idx], r["dx"][idx])
+    del t, r
+    g.sweep(1)
+    o.sweep(1)
+    _same_graph(g, o)
+    assert np.array_equal(g.colours().astype(np.int32), o.colours())
+    assert np.array_equal(g.spins(), o.spins())
+    og, oo = g.observables(), o.observables()
+    assert og["kw_rounds"] == oo["kw_rounds"]
+    _same_energy(og["e_switched"], oo["e_switched"], g.N)
