@@ -44,6 +44,11 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
 __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ __forceinline__ int ld_status(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -87,7 +92,8 @@ __global__ void __launch_bounds__(256) k_kw_level(uint32_t N, uint32_t g, unsign
                                                   const uint32_t* __restrict__ col,
                                                   unsigned long long* word,
                                                   DevCounters* __restrict__ cnt,
-                                                  unsigned long long pass_limit) {
+                                                  unsigned long long ns_limit) {
+  const unsigned long long t_start = global_ns();
   const uint32_t half = g << (p - 1);
   const uint32_t ngroups = (uint32_t)(((unsigned long long)N + ((unsigned long long)g << p) - 1) /
                                       ((unsigned long long)g << p));
@@ -146,7 +152,10 @@ __global__ void __launch_bounds__(256) k_kw_level(uint32_t N, uint32_t g, unsign
       rmax = max(rmax, rv + 1);
       st_relaxed(&word[v], pack(p, rv + 1, c));
     }
-    if (pending && (pass > pass_limit || ld_status(&cnt->status) != 0)) {
+    // bounded wait: give up (status SCO_ETIMEOUT) after ns_limit of wall time or when another
+    // thread already failed
+    if (pending && ((pass & 15) == 15) &&
+        (global_ns() - t_start > ns_limit || ld_status(&cnt->status) != 0)) {
       atomicCAS(&cnt->status, 0, kStatusTimeout);
       break;
     }
@@ -230,13 +239,13 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   const int64_t want = (N / 2 + 255) / 256;
   int64_t grid = (int64_t)blocks_per_sm * num_sms();
   if (want < grid) grid = want > 0 ? want : 1;
-  const unsigned long long pass_limit = 1ull << 26;
+  const unsigned long long ns_limit = 2000000000ull;  // 2 s per level
   unsigned long long magic = 0xFFFFFFFFFFFFFFFFull / g + 1ull;
   for (unsigned p = 1; p <= M; ++p) {
     uint32_t Nn = (uint32_t)N;
     uint32_t gg = g;
     unsigned pp = p;
-    unsigned long long lim = pass_limit;
+    unsigned long long lim = ns_limit;
     void* args[] = {(void*)&Nn, (void*)&gg, (void*)&magic, (void*)&pp, (void*)&row_ptr,
                     (void*)&col, (void*)&b.word, (void*)&cnt, (void*)&lim};
     e = cudaLaunchCooperativeKernel((const void*)k_kw_level, dim3((unsigned)grid), dim3(256),
