@@ -145,6 +145,28 @@ sco_status sco_set_state(sco_ctx* c, const void* buf, size_t len);
 sco_status sco_set_timing(sco_ctx* c, int32_t enable);
 sco_status sco_get_timing(sco_ctx* c, double ms[3], int64_t calls[3]);
 
+/* Allocation-free colouring.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let a library allocate device memory while they run, for example an
+ * application whose device memory is entirely carved up by its own pool allocator, or a
+ * time-critical loop that must not pay for cudaMalloc/cudaFree (cudaFree synchronises the
+ * whole device) or risk an allocation failure half-way through.
+ *
+ * Colours the caller's symmetric CSR graph exactly as sco_colour does (same colours, same
+ * t_R; bit 31 of col entries is ignored).  row_ptr (n + 1), col and colour (n) are device
+ * pointers owned by the caller; max_degree and rounds are optional host pointers.  The
+ * working memory is one fixed device array inside the library, sized for
+ * n <= SCO_KW_STATIC_MAX_VERTICES (8 MiB + 512 B, held on every device that loads the
+ * library until the process exits); larger n returns SCO_EINVAL before any device work.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * and the launch occupancy; make that first call before any stream capture.  Every call
+ * reuses the same array (the control block is cleared on each call), so calls that overlap
+ * on the GPU, from any stream or thread, race: serialise them.  Synchronises `stream`;
+ * returns SCO_ETIMEOUT if a bounded device-side wait gave up.  No allocation of any kind. */
+#define SCO_KW_STATIC_MAX_VERTICES (1 << 20)
+sco_status sco_kw_colour_static(const uint32_t* row_ptr, const uint32_t* col, int64_t n,
+                                int32_t variant, uint32_t* colour, int32_t* max_degree,
+                                int32_t* rounds, void* stream);
+
 /* Waits for the context's stream; returns the sticky device status. */
 sco_status sco_sync(sco_ctx* c);
 

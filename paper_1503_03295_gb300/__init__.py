@@ -15,6 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libsco.so")
 
 SCO_OK, SCO_EINVAL, SCO_ENOMEM, SCO_ECUDA, SCO_ETIMEOUT, SCO_ESTATE, SCO_EGUARD, SCO_ECAPACITY = range(8)
+KW_STATIC_MAX_VERTICES = 1 << 20
 FP64, FP32_GUARDED = 0, 1
 EXCH_ONLY = 0x80000000
 
@@ -77,6 +78,8 @@ def load():
         "sco_set_timing": ([vp, C.c_int32], st),
         "sco_get_timing": ([vp, vp, vp], st),
         "sco_sync": ([vp], st),
+        "sco_kw_colour_static": ([vp, vp, C.c_int64, C.c_int32, vp, C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32), vp], st),
         "sco_strerror": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -101,6 +104,17 @@ def _ptr(a):
 def _check(status, what):
     if status != SCO_OK:
         raise ScoError(status, what)
+
+
+def kw_colour_static(row_ptr_dev, col_dev, n, colour_dev, variant=0, stream=None):
+    """Allocation-free colouring of a caller's CSR graph held in device memory (raw device
+    pointers as ints).  Returns (max_degree, t_R).  See sco_kw_colour_static in sco.h."""
+    d, r = C.c_int32(0), C.c_int32(0)
+    _check(load().sco_kw_colour_static(C.c_void_p(row_ptr_dev), C.c_void_p(col_dev), int(n),
+                                       int(variant), C.c_void_p(colour_dev), C.byref(d),
+                                       C.byref(r), C.c_void_p(stream or 0)),
+           "sco_kw_colour_static")
+    return d.value, r.value
 
 
 def make_params(Lx, Ly=None, T=1.0, D=1.0, J=0.0, seed=0, n_sw=1, precision=FP64,

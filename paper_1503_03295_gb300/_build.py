@@ -14,7 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libsco.so")
-SOURCES = ["api.cu", "scan.cu", "table.cu", "spins.cu", "switch.cu", "colour.cu", "sweep.cu"]
+SOURCES = ["api.cu", "scan.cu", "table.cu", "spins.cu", "switch.cu", "colour.cu", "sweep.cu",
+           "kw_static.cu"]
 HEADERS = ["sco_device.cuh", "sco_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
