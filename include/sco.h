@@ -120,8 +120,9 @@ sco_status sco_get_sizes(sco_ctx* c, int64_t* n_sites, int64_t* n_entries, int32
 /* Host copies of the graph: row_ptr (N + 1), col (n_entries), colour (N); NULL skips. */
 sco_status sco_get_graph(sco_ctx* c, uint32_t* row_ptr, uint32_t* col, uint32_t* colour);
 
-/* Host copies of the colour classes: perm (N sites grouped by colour; order inside a class
- * unspecified) and off (palette + 1 offsets). */
+/* Host copies of the colour classes: perm (N sites sorted by (colour, index); for palettes
+ * above 12288 colours the order inside a class is unspecified) and off (palette + 1
+ * offsets). */
 sco_status sco_get_classes(sco_ctx* c, uint32_t* perm, uint32_t* off);
 
 /* Accept bit per site of the last MC step (N bytes, host). */
@@ -153,7 +154,8 @@ sco_status sco_get_timing(sco_ctx* c, double ms[3], int64_t calls[3]);
  *
  * Colours the caller's symmetric CSR graph exactly as sco_colour does (same colours, same
  * t_R; bit 31 of col entries is ignored).  row_ptr (n + 1), col and colour (n) are device
- * pointers owned by the caller; max_degree and rounds are optional host pointers.  The
+ * pointers owned by the caller (col non-NULL even for a graph without edges); max_degree
+ * and rounds are optional host pointers.  The
  * working memory is one fixed device array inside the library, sized for
  * n <= SCO_KW_STATIC_MAX_VERTICES (8 MiB + 512 B, held on every device that loads the
  * library until the process exits); larger n returns SCO_EINVAL before any device work.

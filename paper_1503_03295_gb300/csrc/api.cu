@@ -69,6 +69,7 @@ struct sco_ctx {
   ColourBufs cb{};
   uint32_t cls_cap = 0;  // capacity of hist / off / cursor
   uint8_t* acc = nullptr;
+  uint32_t* defer = nullptr;  // N sites whose decision goes to the warp-parallel resolve
   DevCounters* cnt = nullptr;   // device
   DevCounters* hcnt = nullptr;  // pinned mirror
   int64_t t = 0;
@@ -182,13 +183,19 @@ sco_status do_colour(sco_ctx* c) {
     cudaFree(c->cb.off);
     cudaFree(c->cb.cursor);
     cudaFree(c->cb.scan_tmp);
-    c->cb.hist = c->cb.off = c->cb.cursor = nullptr;
+    cudaFree(c->cb.tile_cnt);
+    cudaFree(c->cb.dcnt);
+    c->cb.hist = c->cb.off = c->cb.cursor = c->cb.tile_cnt = c->cb.dcnt = nullptr;
     c->cb.scan_tmp = nullptr;
     const uint32_t cap = c->g + 64;
+    const int64_t ntiles = (c->P.N + kClassTileSites - 1) / kClassTileSites;
+    const int64_t tc = (int64_t)(cap < kMaxStablePalette ? cap : kMaxStablePalette) * ntiles + 1;
     SCO_TRY(cudaMalloc(&c->cb.hist, (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.off, (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.cursor, (cap + 1) * sizeof(uint32_t)));
-    SCO_TRY(cudaMalloc(&c->cb.scan_tmp, scan_tmp_bytes(cap + 1)));
+    SCO_TRY(cudaMalloc(&c->cb.dcnt, (cap + 1) * sizeof(uint32_t)));
+    SCO_TRY(cudaMalloc(&c->cb.tile_cnt, tc * sizeof(uint32_t)));
+    SCO_TRY(cudaMalloc(&c->cb.scan_tmp, scan_tmp_bytes(tc > cap + 1 ? tc : cap + 1)));
     c->cls_cap = cap;
   }
   SCO_TRY(kw_run(c->P, c->row_ptr, c->col, c->g, c->p.colour_variant, c->cb, c->cnt, c->st,
@@ -224,13 +231,16 @@ void free_all(sco_ctx* c) {
   cudaFree(c->row_ptr);
   cudaFree(c->col);
   cudaFree(c->cb.word);
+  cudaFree(c->cb.blk);
   cudaFree(c->cb.colour);
   cudaFree(c->cb.hist);
   cudaFree(c->cb.off);
   cudaFree(c->cb.cursor);
   cudaFree(c->cb.perm);
+  cudaFree(c->cb.tile_cnt);
   cudaFree(c->cb.scan_tmp);
   cudaFree(c->acc);
+  cudaFree(c->defer);
   cudaFree(c->cnt);
   if (c->hcnt) cudaFreeHost(c->hcnt);
   for (auto& e : c->evs) {
@@ -289,6 +299,9 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   P.D = p->D;
   P.beta = 1.0 / p->T;
   P.bD = P.beta * p->D;
+  P.inv_bD58 = P.bD > 0.0 ? 0x1p58 / P.bD : 0.0;
+  P.inv_bD58_f = (float)P.inv_bD58;
+  P.lx_magic = div_magic((unsigned long long)p->Lx);
   P.key0 = p->seed;
   P.key1 = (uint64_t)(uint32_t)p->replica;
   const dd l2 = ln2_dd();
@@ -316,9 +329,11 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->sw.scan_tmp, scan_tmp_bytes(N + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->row_ptr, (N + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.word, N * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cb.blk, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.colour, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.perm, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->acc, N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->defer, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cnt, sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMallocHost(&c->hcnt, sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, sizeof(DevCounters), c->st);
@@ -368,8 +383,8 @@ sco_status sco_sweep(sco_ctx* c, int32_t n_mcs) {
     {
       PhaseTimer tm(c, kPhSweep);
       SCO_TRY(sweep_run(c->P, c->tab, c->s, c->s32, c->row_ptr, c->col, c->cb.perm, c->cb.off,
-                        c->g, (uint64_t)c->t, c->p.precision, c->acc, c->cnt, c->st,
-                        &c->launches));
+                        c->g, (uint64_t)c->t, c->p.precision, c->acc, c->defer, c->cb.dcnt,
+                        c->cnt, c->st, &c->launches));
     }
     c->t++;
   }

@@ -13,8 +13,8 @@
 // previous colour, all of them final.  The result therefore does not depend on the order
 // in which ready vertices are processed, and the synchronous round of a vertex is one more
 // than the largest round among those larger neighbours.  Each level runs as one persistent
-// cooperative kernel in which every thread repeatedly visits its own vertices and
-// recolours those whose larger neighbours are done: no grid-wide barrier between rounds,
+// cooperative kernel in which every thread recolours its own vertices once their larger
+// neighbours are done: no grid-wide barrier between rounds,
 // same colours as the synchronous rounds, and t_R recovered from the per-vertex rounds.
 #include <cstdint>
 
@@ -55,15 +55,18 @@ __device__ __forceinline__ int ld_status(const int* p) {
   return v;
 }
 
-__global__ void k_kw_init(int64_t N, uint32_t g, unsigned long long* __restrict__ word) {
+__global__ void k_kw_init(int64_t N, uint32_t g, unsigned long long* __restrict__ word,
+                          uint32_t* __restrict__ blk) {
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (v < N) word[v] = pack(0, 0, (unsigned)(v % g));
+  if (v < N) {
+    word[v] = pack(0, 0, (unsigned)(v % g));
+    blk[v] = 0xFFFFFFFFu;
+  }
 }
 
-// floor(u / g) for 32-bit u and g by one 64-bit high multiply with M = floor((2^64-1)/g) + 1
-// (Lemire, Kaser and Kurz, "Faster remainder by direct computation", 2019).
+// floor(u / g) through the multiplier of g (see div_by_magic).
 __device__ __forceinline__ uint32_t fdiv(uint32_t u, unsigned long long M) {
-  return (uint32_t)__umul64hi(M, (unsigned long long)u);
+  return div_by_magic(u, M);
 }
 
 // Smallest colour in [0, g) not held by a ready same-group neighbour (mex <= degree).
@@ -87,10 +90,86 @@ __device__ __noinline__ unsigned mex_slow(uint32_t v, unsigned p, unsigned long 
   }
 }
 
-__global__ void __launch_bounds__(256) k_kw_level(uint32_t N, uint32_t g, unsigned long long M,
+// One KW level.  Thread t owns the right-half slots r = t + k * nthreads.  It passes over
+// its unfinished vertices again and again: a vertex whose recorded blocker (a larger
+// same-group right-half neighbour not yet recoloured at this level) is still unfinished
+// costs one load; otherwise its row is scanned, and it either records the unfinished
+// larger neighbour of smallest colour (the one likely to finish last) or takes the
+// smallest colour not held by a finished same-group neighbour.  Nothing ever blocks a
+// thread, so with every thread resident the unfinished vertex of largest colour in each
+// group always progresses.
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t kw_vertex(uint32_t r, uint32_t half, unsigned p,
+                                              unsigned long long M) {
+  const uint32_t k = fdiv(r, M) >> (p - 1);  // right half number k, in group k
+  return (2 * k + 1) * half + (r - k * half);
+}
+
+// Returns kNone once v is recoloured, else the index of the neighbour to wait for.
+__device__ __noinline__ uint32_t kw_attempt(uint32_t v, uint32_t cv, unsigned p,
+                                               unsigned long long M,
+                                               const uint32_t* __restrict__ row_ptr,
+                                               const uint32_t* __restrict__ col,
+                                               unsigned long long* word, unsigned& rmax) {
+  const uint32_t grp = fdiv(v, M) >> p;
+  const uint32_t b = row_ptr[v], e = row_ptr[v + 1];
+  unsigned long long used[4] = {0, 0, 0, 0};  // colours < 256 (mex <= degree)
+  unsigned rv = 0;
+  uint32_t wait_u = kNone, wait_c = 0xFFFFFFFFu;
+  // the row in chunks of 8: indices, then the words of the same-group ones, back to back
+  for (uint32_t q0 = b; q0 < e; q0 += 8) {
+    uint32_t uu[8];
+    unsigned long long ww[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) uu[a] = q0 + a < e ? (col[q0 + a] & kIndexMask) : kNone;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      ww[a] = 0;
+      if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) ww[a] = ld_relaxed(&word[uu[a]]);
+      else uu[a] = kNone;
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if (uu[a] == kNone) continue;
+      const unsigned long long wu = ww[a];
+      const uint32_t cu = (uint32_t)(wu & kColMask);
+      const bool right = (fdiv(uu[a], M) >> (p - 1)) & 1u;
+      if (right && tag_of(wu) != p) {
+        // larger: must finish first; smaller: its colour is >= g for now and it waits for v
+        if (cu > cv && cu < wait_c) {
+          wait_c = cu;
+          wait_u = uu[a];
+        }
+        continue;
+      }
+      if (right) rv = max(rv, rnd_of(wu));
+      if (cu < 256) used[cu >> 6] |= 1ull << (cu & 63);
+    }
+  }
+  if (wait_u != kNone) return wait_u;
+  unsigned cn = 0;
+  if (e - b < 256) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (~used[w]) {
+        cn = 64 * w + __ffsll((long long)~used[w]) - 1;
+        break;
+      }
+    }
+  } else {
+    cn = mex_slow(v, p, M, row_ptr, col, word);
+  }
+  rmax = max(rmax, rv + 1);
+  st_relaxed(&word[v], pack(p, rv + 1, cn));
+  return kNone;
+}
+
+__global__ void __launch_bounds__(256, 4) k_kw_level(uint32_t N, uint32_t g, unsigned long long M,
                                                   unsigned p, const uint32_t* __restrict__ row_ptr,
                                                   const uint32_t* __restrict__ col,
                                                   unsigned long long* word,
+                                                  uint32_t* __restrict__ blk,
                                                   DevCounters* __restrict__ cnt,
                                                   unsigned long long ns_limit) {
   const unsigned long long t_start = global_ns();
@@ -100,65 +179,225 @@ __global__ void __launch_bounds__(256) k_kw_level(uint32_t N, uint32_t g, unsign
   const uint32_t R = ngroups * half;  // right-half slots (some beyond N)
   const uint32_t nth = gridDim.x * blockDim.x;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t m = R > tid ? (R - tid + nth - 1) / nth : 0;  // owned slots
   unsigned rmax = 0;
-  bool pending = true;
-  for (unsigned long long pass = 0; pending; ++pass) {
-    pending = false;
-    for (uint32_t r = tid; r < R; r += nth) {
-      const uint32_t k = fdiv(r, M) >> (p - 1);  // right half number k -> group k
-      const uint32_t v = (2 * k + 1) * half + (r - k * half);
-      if (v >= N) continue;
-      const unsigned long long wv = ld_relaxed(&word[v]);
-      if (tag_of(wv) == p) continue;
-      const uint32_t cv = (uint32_t)(wv & kColMask);
-      const uint32_t grp = k;  // v / (g 2^p)
-      const uint32_t b = row_ptr[v], e = row_ptr[v + 1];
-      unsigned long long used[4] = {0, 0, 0, 0};  // colours < 256 (mex <= degree)
-      bool blocked = false;
-      unsigned rv = 0;
-      for (uint32_t q = b; q < e; ++q) {
-        const uint32_t u = col[q] & kIndexMask;
-        const uint32_t gu = fdiv(u, M);
-        if ((gu >> p) != grp) continue;
-        const unsigned long long wu = ld_relaxed(&word[u]);
-        const uint32_t cu = (uint32_t)(wu & kColMask);
-        const bool right = (gu >> (p - 1)) & 1u;
-        if (right && tag_of(wu) != p) {
-          if (cu > cv) {  // larger same-group neighbour still in [g, 2g): wait
-            blocked = true;
-            break;
-          }
-          continue;  // smaller one: its colour is >= g for now and it waits for v
+  unsigned nap = 64;  // back-off (ns) while nothing of this thread can progress
+  if (m <= 32) {
+    // one bit per unfinished owned vertex: waiting passes touch only pending vertices
+    uint32_t vtx[32];
+    unsigned pend = 0;
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      vtx[a] = kNone;
+      if ((uint32_t)a < m) {
+        const uint32_t v = kw_vertex(tid + a * nth, half, p, M);
+        if (v < N) {
+          vtx[a] = v;
+          pend |= 1u << a;
         }
-        if (right) rv = max(rv, rnd_of(wu));
-        if (cu < 256) used[cu >> 6] |= 1ull << (cu & 63);
       }
-      if (blocked) {
-        pending = true;
-        continue;
+    }
+    for (unsigned long long pass = 0; pend; ++pass) {
+      bool progress = false;
+      unsigned todo = pend;
+      while (todo) {
+        const int a = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t v = vtx[a];
+        const uint32_t b = blk[v];
+        if (b != kNone && tag_of(ld_relaxed(&word[b])) != p) continue;  // blocker unfinished
+        const uint32_t w = kw_attempt(v, (uint32_t)(word[v] & kColMask), p, M, row_ptr, col,
+                                      word, rmax);
+        blk[v] = w;
+        if (w == kNone) {
+          pend &= ~(1u << a);
+          progress = true;
+        }
       }
-      unsigned c = 0;
-      if (e - b < 256) {
+      if (!pend) break;
+      if (progress) {
+        nap = 64;
+      } else {
+        __nanosleep(nap);
+        nap = nap < 2048 ? 2 * nap : 2048;
+      }
+      if ((pass & 15) == 15 &&
+          (global_ns() - t_start > ns_limit || ld_status(&cnt->status) != 0)) {
+        // bounded wait: give up (SCO_ETIMEOUT) after ns_limit or once another thread failed
+        atomicCAS(&cnt->status, 0, kStatusTimeout);
+        break;
+      }
+    }
+  } else {
+    // many vertices per thread (very large lattices): every pass visits all owned slots
+    bool pending = true;
+    for (unsigned long long pass = 0; pending; ++pass) {
+      pending = false;
+      bool progress = false;
+      for (uint32_t k = 0; k < m; ++k) {
+        const uint32_t v = kw_vertex(tid + k * nth, half, p, M);
+        if (v >= N) continue;
+        const unsigned long long wv = word[v];
+        if (tag_of(wv) == p) continue;
+        const uint32_t b = blk[v];
+        if (b != kNone && tag_of(ld_relaxed(&word[b])) != p) {
+          pending = true;
+          continue;
+        }
+        const uint32_t w = kw_attempt(v, (uint32_t)(wv & kColMask), p, M, row_ptr, col, word,
+                                      rmax);
+        blk[v] = w;
+        if (w == kNone) progress = true;
+        else pending = true;
+      }
+      if (!pending) break;
+      if (progress) {
+        nap = 64;
+      } else {
+        __nanosleep(nap);
+        nap = nap < 2048 ? 2 * nap : 2048;
+      }
+      if ((pass & 15) == 15 &&
+          (global_ns() - t_start > ns_limit || ld_status(&cnt->status) != 0)) {
+        atomicCAS(&cnt->status, 0, kStatusTimeout);
+        break;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmax = max(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
+  if ((threadIdx.x & 31) == 0 && rmax) atomicMax(&cnt->lev_rounds[p & 31], rmax);
+}
+
+// Block-phased KW level (the default).  Block b owns a contiguous range of right-half
+// slots, buckets its vertices by previous colour in shared memory, and processes the buckets
+// from the largest colour down with a block barrier between colours -- the order of plain
+// BCR, which gives the same colouring.  A larger same-group neighbour owned by another block
+// may still be unfinished: the thread waits for that one word (bounded).  No deadlock: a
+// thread of a block at colour c only waits for a block still at a larger colour, and with
+// every block resident the block at the largest colour never waits.
+__device__ __forceinline__ bool kw_wait(const unsigned long long* word, uint32_t u, unsigned p,
+                                        unsigned long long& wu, unsigned long long t_start,
+                                        unsigned long long ns_limit, DevCounters* cnt) {
+  unsigned spins = 0;
+  unsigned nap = 32;
+  while (tag_of(wu) != p) {
+    __nanosleep(nap);
+    nap = nap < 1024 ? 2 * nap : 1024;
+    wu = ld_relaxed(&word[u]);
+    if ((++spins & 31) == 0 &&
+        (global_ns() - t_start > ns_limit || ld_status(&cnt->status) != 0)) {
+      atomicCAS(&cnt->status, 0, kStatusTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_kw_level_phased(uint32_t N, uint32_t g,
+                                                          unsigned long long M, unsigned p,
+                                                          uint32_t chunk,
+                                                          const uint32_t* __restrict__ row_ptr,
+                                                          const uint32_t* __restrict__ col,
+                                                          unsigned long long* word,
+                                                          DevCounters* __restrict__ cnt,
+                                                          unsigned long long ns_limit) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* ids = sm;              // chunk vertex ids, bucketed by previous colour
+  uint32_t* start = sm + chunk;    // g + 1 bucket starts
+  uint32_t* fill = start + g + 1;  // g bucket cursors
+  __shared__ int abort_flag;
+  const unsigned long long t_start = global_ns();
+  const uint32_t half = g << (p - 1);
+  const uint32_t ngroups = (uint32_t)(((unsigned long long)N + ((unsigned long long)g << p) - 1) /
+                                      ((unsigned long long)g << p));
+  const uint32_t R = ngroups * half;
+  const uint32_t r0 = blockIdx.x * chunk;
+  const uint32_t r1 = min(R, r0 + chunk);
+  if (threadIdx.x == 0) abort_flag = 0;
+  for (uint32_t c = threadIdx.x; c <= g; c += blockDim.x) start[c] = 0;
+  __syncthreads();
+  for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const uint32_t v = kw_vertex(r, half, p, M);
+    if (v < N) atomicAdd(&start[(uint32_t)(word[v] & kColMask) + 1], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive scan of g small counts
+    uint32_t acc = 0;
+    for (uint32_t c = 0; c <= g; ++c) {
+      acc += start[c];
+      start[c] = acc;
+    }
+  }
+  __syncthreads();
+  for (uint32_t c = threadIdx.x; c < g; c += blockDim.x) fill[c] = start[c];
+  __syncthreads();
+  for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const uint32_t v = kw_vertex(r, half, p, M);
+    if (v < N) ids[atomicAdd(&fill[(uint32_t)(word[v] & kColMask)], 1u)] = v;
+  }
+  __syncthreads();
+  unsigned rmax = 0;
+  for (int c = (int)g - 1; c >= 0; --c) {
+    const uint32_t b0 = start[c], b1 = start[c + 1];
+    for (uint32_t q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
+      const uint32_t v = ids[q];
+      const uint32_t cv = (uint32_t)c;
+      const uint32_t grp = fdiv(v, M) >> p;
+      const uint32_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+      unsigned long long used[4] = {0, 0, 0, 0};  // colours < 256 (mex <= degree)
+      unsigned rv = 0;
+      bool ok = true;
+      for (uint32_t q0 = e0; q0 < e1 && ok; q0 += 8) {
+        uint32_t uu[8];
+        unsigned long long ww[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) uu[a] = q0 + a < e1 ? (col[q0 + a] & kIndexMask) : kNone;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          ww[a] = 0;
+          if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) ww[a] = ld_relaxed(&word[uu[a]]);
+          else uu[a] = kNone;
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          if (uu[a] == kNone) continue;
+          unsigned long long wu = ww[a];
+          const bool right = (fdiv(uu[a], M) >> (p - 1)) & 1u;
+          if (right && tag_of(wu) != p) {
+            if ((uint32_t)(wu & kColMask) < cv) continue;  // smaller: colour >= g for now
+            // larger and owned by another block that has not reached it yet
+            if (!kw_wait(word, uu[a], p, wu, t_start, ns_limit, cnt)) {
+              ok = false;
+              break;
+            }
+          }
+          const uint32_t cu = (uint32_t)(wu & kColMask);
+          if (right) rv = max(rv, rnd_of(wu));
+          if (cu < 256) used[cu >> 6] |= 1ull << (cu & 63);
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        break;
+      }
+      unsigned cn = 0;
+      if (e1 - e0 < 256) {
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           if (~used[w]) {
-            c = 64 * w + __ffsll((long long)~used[w]) - 1;
+            cn = 64 * w + __ffsll((long long)~used[w]) - 1;
             break;
           }
         }
       } else {
-        c = mex_slow(v, p, M, row_ptr, col, word);
+        cn = mex_slow(v, p, M, row_ptr, col, word);
       }
       rmax = max(rmax, rv + 1);
-      st_relaxed(&word[v], pack(p, rv + 1, c));
+      st_relaxed(&word[v], pack(p, rv + 1, cn));
     }
-    // bounded wait: give up (status SCO_ETIMEOUT) after ns_limit of wall time or when another
-    // thread already failed
-    if (pending && ((pass & 15) == 15) &&
-        (global_ns() - t_start > ns_limit || ld_status(&cnt->status) != 0)) {
-      atomicCAS(&cnt->status, 0, kStatusTimeout);
-      break;
-    }
+    __syncthreads();
+    if (abort_flag) break;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) rmax = max(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
@@ -198,9 +437,64 @@ __global__ void k_nonempty(uint32_t g, const uint32_t* __restrict__ hist,
   if ((threadIdx.x & 31) == 0 && n) atomicAdd(&cnt->n_colours, n);
 }
 
-// Sites of one colour keep ascending order inside a warp; warps claim their ranges with
-// one atomic per colour and warp.  The order inside a class does not affect the results
-// (sites of one colour never interact).
+// Stable colour classes: tiles of kClassTile sites count their colours, an exclusive scan
+// over (colour, tile) gives every tile its start inside every class, and one warp per tile
+// places the sites in ascending order.  perm is then sites sorted by (colour, index), the
+// order of the oracle, and consecutive threads of a sweep visit neighbouring sites.
+constexpr int kClassTile = (int)kClassTileSites;
+
+__global__ void k_tile_hist(uint32_t N, uint32_t g, uint32_t ntiles,
+                            const uint32_t* __restrict__ colour, uint32_t* __restrict__ tcnt) {
+  extern __shared__ uint32_t h[];
+  for (uint32_t c = threadIdx.x; c < g; c += blockDim.x) h[c] = 0;
+  __syncthreads();
+  const uint32_t v0 = blockIdx.x * kClassTile;
+  const uint32_t v1 = min(N, v0 + kClassTile);
+  for (uint32_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) atomicAdd(&h[colour[v]], 1u);
+  __syncthreads();
+  for (uint32_t c = threadIdx.x; c < g; c += blockDim.x) tcnt[(size_t)c * ntiles + blockIdx.x] = h[c];
+  if (blockIdx.x == 0 && threadIdx.x == 0) tcnt[(size_t)g * ntiles] = 0;
+}
+
+__global__ void __launch_bounds__(32) k_tile_scatter(uint32_t N, uint32_t g, uint32_t ntiles,
+                                                     const uint32_t* __restrict__ colour,
+                                                     const uint32_t* __restrict__ base,
+                                                     uint32_t* __restrict__ perm,
+                                                     uint32_t* __restrict__ off) {
+  extern __shared__ uint32_t run[];
+  const int lane = threadIdx.x;
+  for (uint32_t c = lane; c < g; c += 32) run[c] = base[(size_t)c * ntiles + blockIdx.x];
+  __syncwarp();
+  const uint32_t v0 = blockIdx.x * kClassTile;
+  const uint32_t v1 = min(N, v0 + kClassTile);
+  for (uint32_t vb = v0; vb < v1; vb += 32) {
+    const uint32_t v = vb + lane;
+    const bool ok = v < v1;
+    const uint32_t c = ok ? colour[v] : 0xFFFFFFFFu;
+    const unsigned mask = __match_any_sync(0xffffffffu, c);
+    if (ok) perm[run[c] + __popc(mask & ((1u << lane) - 1u))] = v;
+    __syncwarp();
+    if (ok && lane == __ffs(mask) - 1) run[c] += __popc(mask);
+    __syncwarp();
+  }
+  if (blockIdx.x == 0) {
+    for (uint32_t c = lane; c < g; c += 32) off[c] = base[(size_t)c * ntiles];
+    if (lane == 0) off[g] = N;
+  }
+}
+
+__global__ void k_nonempty_off(uint32_t g, const uint32_t* __restrict__ off,
+                               DevCounters* __restrict__ cnt) {
+  unsigned n = 0;
+  for (uint32_t c = threadIdx.x; c < g; c += blockDim.x) n += off[c + 1] > off[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd(&cnt->n_colours, n);
+}
+
+// Fallback for palettes too large for shared memory: sites keep ascending order inside a
+// warp and warps claim their ranges with atomics (the order inside a class does not affect
+// the results: sites of one colour never interact).
 __global__ void k_scatter(int64_t N, const uint32_t* __restrict__ colour,
                           const uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
                           uint32_t* __restrict__ perm) {
@@ -228,8 +522,50 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   cudaError_t e = cudaMemsetAsync(cnt->lev_rounds, 0, sizeof(cnt->lev_rounds), st);
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((N + 255) / 256);
-  k_kw_init<<<nb, 256, 0, st>>>(N, g, b.word);
+  k_kw_init<<<nb, 256, 0, st>>>(N, g, b.word, b.blk);
   ++*launches;
+  const unsigned long long ns_limit = 2000000000ull;  // 2 s per level
+  unsigned long long magic = div_magic(g);
+  // block-phased levels when every block's bucket of vertices fits in its shared memory
+  constexpr size_t kPhasedSmem = 24 * 1024;  // bytes of dynamic shared memory per block
+  static int phased_bps = 0;
+  if (phased_bps == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&phased_bps, k_kw_level_phased, 256,
+                                                      kPhasedSmem);
+    if (e != cudaSuccess) return e;
+    if (phased_bps < 1) phased_bps = 1;
+  }
+  const int64_t pgrid = (int64_t)phased_bps * num_sms();
+  bool phased = true;
+  int64_t max_chunk = 0;
+  for (unsigned p = 1; p <= M; ++p) {
+    const int64_t gsz = (int64_t)g << p, hf = (int64_t)g << (p - 1);
+    const int64_t R = (N + gsz - 1) / gsz * hf;
+    const int64_t ch = (R + pgrid - 1) / pgrid;
+    if (ch > max_chunk) max_chunk = ch;
+  }
+  const size_t need = (size_t)(max_chunk + 2 * (int64_t)g + 2) * sizeof(uint32_t);
+  if (need > kPhasedSmem) phased = false;
+  if (phased) {
+    for (unsigned p = 1; p <= M; ++p) {
+      const int64_t gsz = (int64_t)g << p, hf = (int64_t)g << (p - 1);
+      const int64_t R = (N + gsz - 1) / gsz * hf;
+      uint32_t chunk = (uint32_t)((R + pgrid - 1) / pgrid);
+      const size_t sh = (size_t)(chunk + 2 * (size_t)g + 2) * sizeof(uint32_t);
+      uint32_t Nn = (uint32_t)N, gg = g;
+      unsigned pp = p;
+      unsigned long long lim = ns_limit;
+      void* args[] = {(void*)&Nn, (void*)&gg, (void*)&magic, (void*)&pp, (void*)&chunk,
+                      (void*)&row_ptr, (void*)&col, (void*)&b.word, (void*)&cnt, (void*)&lim};
+      e = cudaLaunchCooperativeKernel((const void*)k_kw_level_phased, dim3((unsigned)pgrid),
+                                      dim3(256), args, sh, st);
+      if (e != cudaSuccess) return e;
+      ++*launches;
+    }
+    k_kw_final<<<nb, 256, 0, st>>>(N, M, g, variant, b.word, b.colour, cnt);
+    ++*launches;
+    return cudaGetLastError();
+  }
   static int blocks_per_sm = 0;
   if (blocks_per_sm == 0) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_kw_level, 256, 0);
@@ -239,15 +575,13 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   const int64_t want = (N / 2 + 255) / 256;
   int64_t grid = (int64_t)blocks_per_sm * num_sms();
   if (want < grid) grid = want > 0 ? want : 1;
-  const unsigned long long ns_limit = 2000000000ull;  // 2 s per level
-  unsigned long long magic = 0xFFFFFFFFFFFFFFFFull / g + 1ull;
   for (unsigned p = 1; p <= M; ++p) {
     uint32_t Nn = (uint32_t)N;
     uint32_t gg = g;
     unsigned pp = p;
     unsigned long long lim = ns_limit;
     void* args[] = {(void*)&Nn, (void*)&gg, (void*)&magic, (void*)&pp, (void*)&row_ptr,
-                    (void*)&col, (void*)&b.word, (void*)&cnt, (void*)&lim};
+                    (void*)&col, (void*)&b.word, (void*)&b.blk, (void*)&cnt, (void*)&lim};
     e = cudaLaunchCooperativeKernel((const void*)k_kw_level, dim3((unsigned)grid), dim3(256),
                                     args, 0, st);
     if (e != cudaSuccess) return e;
@@ -261,6 +595,23 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
 cudaError_t bucket_run(const DevParams& P, uint32_t g, ColourBufs& b, DevCounters* cnt,
                        cudaStream_t st, int64_t* launches) {
   const int64_t N = P.N;
+  const uint32_t ntiles = (uint32_t)((N + kClassTile - 1) / kClassTile);
+  if (g <= kMaxStablePalette) {
+    cudaError_t e = cudaMemsetAsync(&cnt->n_colours, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    const size_t sh = (size_t)g * sizeof(uint32_t);
+    k_tile_hist<<<ntiles, 256, sh, st>>>((uint32_t)N, g, ntiles, b.colour, b.tile_cnt);
+    ++*launches;
+    e = scan_excl_u32(b.tile_cnt, b.tile_cnt, (int64_t)g * ntiles + 1, b.scan_tmp, nullptr, st,
+                      launches);
+    if (e != cudaSuccess) return e;
+    k_tile_scatter<<<ntiles, 32, sh, st>>>((uint32_t)N, g, ntiles, b.colour, b.tile_cnt, b.perm,
+                                          b.off);
+    ++*launches;
+    k_nonempty_off<<<1, 1024, 0, st>>>(g, b.off, cnt);
+    ++*launches;
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemsetAsync(b.hist, 0, (g + 1) * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.cursor, 0, g * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(&cnt->n_colours, 0, sizeof(unsigned), st);

@@ -27,7 +27,7 @@ struct StaticCtrl {
   unsigned int g;
   unsigned int levels;
   int status;
-  unsigned long long magic;  // floor((2^64 - 1) / g) + 1
+  unsigned long long magic;  // multiplier of g (div_magic)
   unsigned int kw_rounds;
   unsigned int pad;
   unsigned int lev_rounds[32];
@@ -63,7 +63,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 __device__ __forceinline__ uint32_t fdiv(uint32_t u, unsigned long long M) {
-  return (uint32_t)__umul64hi(M, (unsigned long long)u);
+  return div_by_magic(u, M);  // M = 0 stands for g = 1
 }
 
 __global__ void k_st_degree(uint32_t n, const uint32_t* __restrict__ row_ptr,
@@ -82,7 +82,7 @@ __global__ void k_st_setup(uint32_t n, StaticCtrl* __restrict__ ctrl) {
   while ((1u << M) < G) ++M;
   ctrl->g = g;
   ctrl->levels = M;
-  ctrl->magic = 0xFFFFFFFFFFFFFFFFull / g + 1ull;
+  ctrl->magic = div_magic(g);
 }
 
 __global__ void k_st_init(uint32_t n, unsigned long long* __restrict__ word,

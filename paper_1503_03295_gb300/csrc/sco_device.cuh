@@ -20,9 +20,27 @@ struct DevParams {
   int64_t N;        // Lx * Ly
   int64_t K;        // half-plane displacement count
   double J, D, beta, bD;  // beta = fl(1/T), bD = fl(beta * D)
+  double inv_bD58;        // fl(2^58 / bD): exponential draw -> hazard prefix units
+  float inv_bD58_f;       // its FP32 rounding
   uint64_t key0, key1;    // Philox key: seed, replica
   double ln2_hi, ln2_lo;  // ln 2 as a double-double
+  unsigned long long lx_magic;  // floor((2^64 - 1) / Lx) + 1 (0 when Lx = 1)
 };
+
+// floor(u / d) for 32-bit u and d >= 2 by one 64-bit high multiply with
+// M = floor((2^64 - 1) / d) + 1 (Lemire, Kaser and Kurz, "Faster remainder by direct
+// computation", 2019); M = 0 stands for d = 1.
+__host__ __device__ __forceinline__ unsigned long long div_magic(unsigned long long d) {
+  return d > 1 ? 0xFFFFFFFFFFFFFFFFull / d + 1ull : 0ull;
+}
+__device__ __forceinline__ uint32_t div_by_magic(uint32_t u, unsigned long long M) {
+  return M ? (uint32_t)__umul64hi(M, (unsigned long long)u) : u;
+}
+
+// Row y = i / Lx of site i, keeping 64-bit integer division out of the inner loops.
+__device__ __forceinline__ uint32_t site_row(uint32_t i, const DevParams& P) {
+  return div_by_magic(i, P.lx_magic);
+}
 
 // ---------------------------------------------------------------------------------------
 // Philox4x64-10, Salmon, Moraes, Dror and Shaw (SC'11): two 64x64->128 multiplies per round
@@ -174,8 +192,14 @@ __host__ __device__ inline dd dd_expm1_small(dd x) {
   const dd y = dd_ldexp(x, -10);
   dd term = y, sum = y;
   for (int n = 2; n <= 14; ++n) {
-    term = dd_mul(term, y);
-    term = dd_div(term, dd_from((double)n));
+    // 1/n as a double-double: h = fl(1/n), l = (1 - n h) / n with the residual exact by FMA
+    const double h = 1.0 / n;
+#ifdef __CUDA_ARCH__
+    const dd inv = {h, __fma_rn(-(double)n, h, 1.0) / n};
+#else
+    const dd inv = {h, __builtin_fma(-(double)n, h, 1.0) / n};
+#endif
+    term = dd_mul(dd_mul(term, y), inv);
     sum = dd_add(sum, term);
   }
   for (int k = 0; k < 10; ++k) sum = dd_add(dd_ldexp(sum, 1), dd_mul(sum, sum));

@@ -43,7 +43,10 @@ struct Table {
   uint32_t* disp = nullptr;  // packed (dx & 0xFFFF) | (dy << 16), sorted by (r^2, dy, dx)
   uint64_t* W = nullptr;     // inclusive prefix of the integer hazards A_m
   double2* xy = nullptr;     // by (|dx|, |dy|): {fl(D c(r^2)), V_max = fl(fl(D A) 2^-59)}
-  float4* xy32 = nullptr;    // by (|dx|, |dy|): FP32 copies {Dc, Vmax, 2 beta Vmax, 0}
+  double* xyq = nullptr;     // by (|dx|, |dy|): q = -expm1(-2 beta V_max), candidate probability
+  float4* xy32 = nullptr;    // by (|dx|, |dy|): FP32 copies {Dc, Vmax, 2 beta Vmax, q}
+  double4_32a* sw64 = nullptr;   // sweep, by (|dx|, |dy|): {fl(Dc r^2), fl(3 Dc), fl(beta Vmax), c0}
+  float4* sw32 = nullptr;    // the same in FP32 (with its own c0)
   int32_t m_nn[2] = {-1, -1};
 };
 cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches);
@@ -83,13 +86,18 @@ cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* ro
 // ---- colour.cu ----
 struct ColourBufs {
   unsigned long long* word;  // N packed (level tag, round, colour)
+  uint32_t* blk;     // N neighbour each unfinished vertex waits for (0xFFFFFFFF: none)
   uint32_t* colour;  // N final colours
   uint32_t* hist;    // g + 1
   uint32_t* off;     // g + 1
   uint32_t* cursor;  // g
+  uint32_t* dcnt;    // g deferred sweep decisions per colour
   uint32_t* perm;    // N
+  uint32_t* tile_cnt;  // palette x tiles (+1) per-tile colour counts, scanned in place
   uint64_t* scan_tmp;
 };
+constexpr uint32_t kMaxStablePalette = 12288;  // palettes up to this size get stable classes
+constexpr int64_t kClassTileSites = 2048;
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
                    uint32_t g, int variant, ColourBufs& b, DevCounters* cnt, cudaStream_t st,
                    int64_t* launches);
@@ -100,7 +108,8 @@ cudaError_t bucket_run(const DevParams& P, uint32_t g, ColourBufs& b, DevCounter
 cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,
                       const uint32_t* off, uint32_t g, uint64_t step, int precision,
-                      uint8_t* acc, DevCounters* cnt, cudaStream_t st, int64_t* launches);
+                      uint8_t* acc, uint32_t* defer, uint32_t* dcnt, DevCounters* cnt,
+                      cudaStream_t st, int64_t* launches);
 
 int num_sms();
 

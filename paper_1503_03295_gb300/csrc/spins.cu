@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(256) k_site_obs(DevParams P, const double* __r
     v[0] += x;
     v[1] += y;
     v[2] += z;
-    const int32_t xi = (int32_t)(i % P.Lx), yi = (int32_t)(i / P.Lx);
+    const int32_t yi = (int32_t)site_row((uint32_t)i, P);
+    const int32_t xi = (int32_t)((uint32_t)i - (uint32_t)yi * (uint32_t)P.Lx);
     const double ux = xi - rcx, uy = yi - rcy;
     const double nr = sqrt(ux * ux + uy * uy);
     if (nr > 0.0) v[3] += (x * uy - y * ux) / nr;
@@ -101,14 +102,16 @@ __global__ void __launch_bounds__(256) k_pair_obs(DevParams P, const double* __r
   double v[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t xi = (int32_t)(i % P.Lx), yi = (int32_t)(i / P.Lx);
+    const int32_t yi = (int32_t)site_row((uint32_t)i, P);
+    const int32_t xi = (int32_t)((uint32_t)i - (uint32_t)yi * (uint32_t)P.Lx);
     const double ax = s[i], ay = s[P.N + i], az = s[2 * P.N + i];
     for (uint32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
       const uint32_t c = col[e];
       if (c & kExchOnly) continue;
       const int64_t j = c;
       if (j <= i) continue;
-      const int32_t dx = (int32_t)(j % P.Lx) - xi, dy = (int32_t)(j / P.Lx) - yi;
+      const uint32_t yj = site_row((uint32_t)j, P);
+      const int32_t dx = (int32_t)((uint32_t)j - yj * (uint32_t)P.Lx) - xi, dy = (int32_t)yj - yi;
       const double2 t = xy[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
       const double V = pair_V(t.x, (double)dx * dx + (double)dy * dy, ax, ay, az, s[j],
                               s[P.N + j], s[2 * P.N + j], (double)dx, (double)dy);

@@ -83,11 +83,12 @@ __device__ __forceinline__ int64_t next_candidate(const DevParams& P, const Near
                                                   uint64_t wE, unsigned& ghits) {
   if (s >= T.K - 1 || !(P.bD > 0.0)) return T.K;
   const double up = u53pos(wE);
-  const double tau = (-log(up) / P.bD) * 0x1p58;
+  const double tau = -log(up) * P.inv_bD58;
   const uint64_t rem = Wtot - Ws;
   int64_t k = T.K;
   if (tau <= (double)rem) k = T.lower_bound(s + 1, Ws + __double2ull_ru(tau));
-  // tau carries < 2^-49 relative error (log, fl(beta D), one division): guard at 2^-46
+  // tau carries < 2^-49 relative error (log, fl(beta D), fl(2^58 / bD), one product): guard
+  // at 2^-46
   const double eps = 0x1p-46;
   bool certain = true;
   if (k < T.K && !((double)(T.w(k) - Ws) >= tau * (1.0 + eps))) certain = false;
@@ -95,6 +96,58 @@ __device__ __forceinline__ int64_t next_candidate(const DevParams& P, const Near
   if (certain) return k;
   ++ghits;
   return next_candidate_dd(P, T, s, Ws, up);
+}
+
+// ceil(x) as an integer for finite x >= 0 (saturating at 2^64 - 1), from the bits of x with
+// integer operations only (64-bit conversions would run on the FP64 pipe).
+__device__ __forceinline__ uint64_t ceil_u64(float x) {
+  const uint32_t b = __float_as_uint(x);
+  if (b == 0u || (b >> 31)) return 0ull;
+  const int ex = (int)((b >> 23) & 0xFFu) - 150;  // x = mant * 2^ex
+  const uint64_t mant = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
+  if (ex >= 0) return ex >= 40 ? ~0ull : mant << ex;
+  if (ex <= -25) return 1ull;  // 0 < x < 1
+  const uint64_t q = mant >> (-ex);
+  return q + ((q << (-ex)) != mant ? 1ull : 0ull);
+}
+
+// FP32 screen of the candidate search.  E = -ln u+ is taken as -log1pf(-(1 - u+)) above 1/2
+// (1 - u+ is an exact integer times 2^-53) and -logf(u+) below, so its relative error stays
+// below 2^-20.5 (one input rounding, 4 ulp of the function); tau = E fl32(2^58 / bD) adds
+// two roundings.  Margins inside 2^-18 fall through to the FP64 search.  All comparisons
+// with the uint64 prefix W are made in integers.
+__device__ __forceinline__ int64_t next_candidate_fp32(const DevParams& P, const NearTable& T,
+                                                       int64_t s, uint64_t Ws, uint64_t Wtot,
+                                                       uint64_t wE, unsigned& g32,
+                                                       unsigned& ghits) {
+  if (s >= T.K - 1 || !(P.bD > 0.0)) return T.K;
+  const uint64_t m53 = wE >> 11;  // u+ = (m53 + 1) 2^-53
+  float E;
+  if (m53 >= (1ull << 52)) {
+    const uint64_t dm = (1ull << 53) - 1ull - m53;  // < 2^52
+    const float d = __uint2float_rn((uint32_t)(dm >> 20)) * 0x1p-33f +
+                    __uint2float_rn((uint32_t)(dm & 0xFFFFFu)) * 0x1p-53f;
+    E = -log1pf(-d);
+  } else {
+    const uint64_t um = m53 + 1ull;  // <= 2^52
+    const float u = __uint2float_rn((uint32_t)(um >> 20)) * 0x1p-33f +
+                    __uint2float_rn((uint32_t)(um & 0xFFFFFu)) * 0x1p-53f;
+    E = -logf(u);
+  }
+  const float tau = E * P.inv_bD58_f;
+  const float eps = 0x1p-18f;
+  const uint64_t rem = Wtot - Ws;
+  const uint64_t thr = ceil_u64(tau);
+  int64_t k = T.K;
+  if (thr <= rem) k = T.lower_bound(s + 1, Ws + thr);
+  const uint64_t hi = ceil_u64(tau * (1.0f + eps));  // W_k - W_s >= hi: surely a candidate
+  const uint64_t lo = ceil_u64(tau * (1.0f - eps));  // W_k-1 - W_s < lo: surely not
+  bool certain = tau < 0x1p62f;
+  if (k < T.K && T.w(k) - Ws < hi) certain = false;
+  if (k - 1 > s && T.w(k - 1) - Ws >= lo) certain = false;
+  if (certain) return k;
+  ++g32;
+  return next_candidate(P, T, s, Ws, Wtot, wE, ghits);
 }
 
 // Exact survival test u q < 1 - P_ij in double-double.
@@ -113,16 +166,14 @@ __device__ __noinline__ bool survives_dd(const DevParams& P, const double* Si, c
 
 // FP64 survival test with its error bound: |dV| <= 2^-47 Dc r^2, fl(Vmax) within 2^-52,
 // expm1 within 4 ulp, so 1 - P and q within the terms below (doubled for margin).
-__device__ __forceinline__ bool survives_fp64(const DevParams& P, double Dc, double Vm,
+__device__ __forceinline__ bool survives_fp64(const DevParams& P, double Dc, double Vm, double q,
                                               double r2, const double* Si, const double* Sj,
                                               int32_t dx, int32_t dy, uint64_t A, double u1,
                                               unsigned& ghits) {
   const double V = pair_V(Dc, r2, Si[0], Si[1], Si[2], Sj[0], Sj[1], Sj[2], (double)dx,
                           (double)dy);
   const double b = P.beta * (V - Vm);
-  const double a = (2.0 * P.beta) * Vm;
-  const double pr = -expm1(b);
-  const double q = -expm1(-a);
+  const double pr = -expm1(b);  // q = -expm1(-fl(2 beta Vmax)) comes from the table
   const double mu = pr - u1 * q;
   const double dV = 0x1p-47 * Dc * r2;
   const double B =
@@ -137,12 +188,14 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, double Dc, dou
 // (|dS| <= 2^-24 per component), table constants rounded to FP32, expm1f within 4 ulp.
 // Falls through to the FP64 test (and from there to double-double) inside the bound.
 __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32, double Dc,
-                                              double Vm, double r2, const float* Si32,
+                                              double Vm, double q64, const float* Si32,
                                               const float* Sj32, const double* Si,
                                               const double* Sj, int32_t dx, int32_t dy,
-                                              uint64_t A, double u1, unsigned& g32,
+                                              uint64_t A, uint64_t wU, unsigned& g32,
                                               unsigned& ghits) {
-  const float fr2 = (float)r2, fx = (float)dx, fy = (float)dy;
+  const float fr2 = (float)(dx * dx + dy * dy), fx = (float)dx, fy = (float)dy;
+  // u truncated to 24 bits: 0 <= u - u24 < 2^-24, inside the 2^-19 q term of the bound
+  const float u24 = __uint2float_rn((uint32_t)(wU >> 40)) * 0x1p-24f;
   const float ss = Si32[0] * Sj32[0] + Si32[1] * Sj32[1] + Si32[2] * Sj32[2];
   const float pa = Si32[0] * fx + Si32[1] * fy;
   const float pb = Sj32[0] * fx + Sj32[1] * fy;
@@ -150,8 +203,8 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32, do
   const float beta = (float)P.beta;
   const float b = beta * (V - t32.y);
   const float pr = -expm1f(b);
-  const float q = -expm1f(-t32.z);
-  const float mu = pr - (float)u1 * q;
+  const float q = t32.w;  // fl32 of the FP64 q: 2^-24 on top of its 4 ulp
+  const float mu = pr - u24 * q;
   // |dV| <= 2^-17 Dc r^2 (shadow spins, FP32 products, constant rounding); beta and the
   // constants carry 2^-24 each; expm1f 4 ulp; generous factor 2.
   const float dV = 0x1p-17f * t32.x * fr2;
@@ -160,13 +213,15 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32, do
   if (mu > B) return true;
   if (mu < -B) return false;
   ++g32;
-  return survives_fp64(P, Dc, Vm, r2, Si, Sj, dx, dy, A, u1, ghits);
+  return survives_fp64(P, Dc, Vm, q64, (double)dx * dx + (double)dy * dy, Si, Sj, dx, dy, A,
+                       u53(wU), ghits);
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(256) k_switch(const DevParams P, const uint64_t* __restrict__ W,
                                                 const uint32_t* __restrict__ disp,
                                                 const double2* __restrict__ xy,
+                                                const double* __restrict__ xyq,
                                                 const float4* __restrict__ xy32,
                                                 const double* __restrict__ s,
                                                 const float* __restrict__ s32, uint32_t epoch,
@@ -186,7 +241,8 @@ __global__ void __launch_bounds__(256) k_switch(const DevParams P, const uint64_
   unsigned ghits = 0, g32 = 0;
   if (i < P.N) {
     const uint64_t Wtot = P.K > 0 ? __ldg(&W[P.K - 1]) : 0;
-    const int32_t xi = (int32_t)(i % P.Lx), yi = (int32_t)(i / P.Lx);
+    const int32_t yi = (int32_t)site_row((uint32_t)i, P);
+    const int32_t xi = (int32_t)((uint32_t)i - (uint32_t)yi * (uint32_t)P.Lx);
     const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
     float Si32[3] = {0.f, 0.f, 0.f};
     if (PREC == 1) {
@@ -219,7 +275,8 @@ __global__ void __launch_bounds__(256) k_switch(const DevParams P, const uint64_
       if ((n & 1) == 0) w = philox((uint64_t)i, epoch, n >> 1, kTagSwitch, P.key0, P.key1);
       const uint64_t wE = (n & 1) ? w.w[2] : w.w[0];
       const uint64_t wU = (n & 1) ? w.w[3] : w.w[1];
-      const int64_t k = next_candidate(P, T, sidx, Ws, Wtot, wE, ghits);
+      const int64_t k = PREC == 1 ? next_candidate_fp32(P, T, sidx, Ws, Wtot, wE, g32, ghits)
+                                  : next_candidate(P, T, sidx, Ws, Wtot, wE, ghits);
       if (k >= P.K) break;
       const uint32_t d = T.d(k);
       const int32_t dx = (int16_t)(d & 0xFFFFu), dy = (int32_t)(d >> 16);
@@ -231,15 +288,14 @@ __global__ void __launch_bounds__(256) k_switch(const DevParams P, const uint64_
         const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
         const double2 t = __ldg(&xy[tix]);
         const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-        const double r2 = (double)dx * dx + (double)dy * dy;
-        const double u1 = u53(wU);
         bool surv;
         if (PREC == 1) {
           const float Sj32[3] = {s32[j], s32[P.N + j], s32[2 * P.N + j]};
-          surv = survives_fp32(P, __ldg(&xy32[tix]), t.x, t.y, r2, Si32, Sj32, Si, Sj, dx, dy,
-                               A, u1, g32, ghits);
+          surv = survives_fp32(P, __ldg(&xy32[tix]), t.x, t.y, __ldg(&xyq[tix]), Si32, Sj32, Si,
+                               Sj, dx, dy, A, wU, g32, ghits);
         } else {
-          surv = survives_fp64(P, t.x, t.y, r2, Si, Sj, dx, dy, A, u1, ghits);
+          surv = survives_fp64(P, t.x, t.y, __ldg(&xyq[tix]), (double)dx * dx + (double)dy * dy,
+                               Si, Sj, dx, dy, A, u53(wU), ghits);
         }
         if (surv) {
           emit((uint32_t)j);
@@ -365,11 +421,11 @@ cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, cons
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((P.N + 255) / 256);
   if (precision == 1)
-    k_switch<1><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.xy, t.xy32, s, s32, epoch, t.m_nn[0],
-                                     t.m_nn[1], b, cnt);
+    k_switch<1><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.xy, t.xyq, t.xy32, s, s32, epoch,
+                                     t.m_nn[0], t.m_nn[1], b, cnt);
   else
-    k_switch<0><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.xy, t.xy32, s, s32, epoch, t.m_nn[0],
-                                     t.m_nn[1], b, cnt);
+    k_switch<0><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.xy, t.xyq, t.xy32, s, s32, epoch,
+                                     t.m_nn[0], t.m_nn[1], b, cnt);
   ++*launches;
   return cudaGetLastError();
 }

@@ -67,8 +67,13 @@ __global__ void k_hazard(int64_t K, const uint32_t* __restrict__ disp, uint64_t*
   A[m] = hazard_A((int64_t)dx * dx + (int64_t)dy * dy);
 }
 
+// Sweep constants of a pair at (|dx|, |dy|): the field of S_j on site i is
+// f = A1 S_j - A3 (S_j.d) d with A1 = fl(Dc r^2), A3 = fl(3 Dc), so V(S) = S.f and
+// x = beta V - fl(beta Vmax).  c0 bounds the part of |x error| that does not scale with |x|:
+// FP64 |dV| <= 2^-46 Dc r^2, FP32 |dV| <= 2^-16 Dc r^2 (shadow spins, FP32 constants).
 __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __restrict__ xy,
-                     float4* __restrict__ xy32) {
+                     double* __restrict__ xyq, float4* __restrict__ xy32,
+                     double4_32a* __restrict__ sw64, float4* __restrict__ sw32) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= (int64_t)Lx * Ly) return;
   const int64_t ax = q % Lx, ay = q / Lx;
@@ -78,8 +83,16 @@ __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __r
     dc = __dmul_rn(D, coupling_c(r2));
     vm = __dmul_rn(__dmul_rn(D, (double)hazard_A(r2)), 0x1p-59);
   }
+  const double a = (2.0 * beta) * vm;
+  const double cq = -expm1(-a);
   xy[q] = make_double2(dc, vm);
-  xy32[q] = make_float4((float)dc, (float)vm, (float)(2.0 * beta * vm), 0.f);
+  xyq[q] = cq;
+  xy32[q] = make_float4((float)dc, (float)vm, (float)a, (float)cq);
+  const double a1 = dc * (double)r2, a3 = 3.0 * dc, bvm = beta * vm;
+  const double c64 = beta * (0x1p-46 * dc * (double)r2) + 0x1p-51 * bvm;
+  const double c32 = beta * (0x1p-16 * dc * (double)r2) + 0x1p-21 * bvm;
+  sw64[q] = make_double4_32a(a1, a3, bvm, c64 * (1.0 + 0x1p-20));
+  sw32[q] = make_float4((float)a1, (float)a3, (float)bvm, (float)(c32 * (1.0 + 0x1p-20)));
 }
 
 }  // namespace
@@ -90,7 +103,11 @@ cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* l
   const int64_t nxy = (int64_t)P.Lx * P.Ly;
   if ((e = cudaMalloc(&t.xy, nxy * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&t.xy32, nxy * sizeof(float4))) != cudaSuccess) return e;
-  k_xy<<<(unsigned)((nxy + 255) / 256), 256, 0, s>>>(P.Lx, P.Ly, P.D, P.beta, t.xy, t.xy32);
+  if ((e = cudaMalloc(&t.xyq, nxy * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&t.sw64, nxy * sizeof(double4_32a))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&t.sw32, nxy * sizeof(float4))) != cudaSuccess) return e;
+  k_xy<<<(unsigned)((nxy + 255) / 256), 256, 0, s>>>(P.Lx, P.Ly, P.D, P.beta, t.xy, t.xyq,
+                                                      t.xy32, t.sw64, t.sw32);
   ++*launches;
   const int64_t K = P.K;
   if ((e = cudaMalloc(&t.disp, (K > 0 ? K : 1) * sizeof(uint32_t))) != cudaSuccess) return e;
@@ -141,6 +158,9 @@ void table_free(Table& t) {
   cudaFree(t.W);
   cudaFree(t.xy);
   cudaFree(t.xy32);
+  cudaFree(t.xyq);
+  cudaFree(t.sw64);
+  cudaFree(t.sw32);
   t = Table();
 }
 

@@ -29,12 +29,14 @@ def test_static_colouring_matches_sco_colour_on_consecutive_calls():
     import torch
 
     stream = torch.cuda.current_stream().cuda_stream
-    cases = [(96, 0.4, 1, 0.0, 1.0, 0), (40, 0.8, 2, 1.0, 0.1, 0), (96, 0.4, 1, 0.0, 1.0, 1)]
+    cases = [(96, 0.4, 1, 0.0, 1.0, 0), (40, 0.8, 2, 1.0, 0.1, 0), (96, 0.4, 1, 0.0, 1.0, 1),
+             (30, 1e12, 3, 0.0, 1.0, 0)]  # the last has no edges: palette of one colour
     for L, T, seed, J, D, variant in cases:
         rp, col, ref, obs = _reference(L, T, seed, J, D, variant)
         n = L * L
         d_rp = torch.from_numpy(rp.view(np.int32).copy()).cuda()
-        d_col = torch.from_numpy(col.view(np.int32).copy()).cuda()
+        # a graph without edges still passes a valid (one-entry) device buffer for col
+        d_col = torch.from_numpy(col.view(np.int32).copy() if col.size else np.zeros(1, np.int32)).cuda()
         out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
         for _ in range(2):  # two calls in a row on the same graph
             out.fill_(-1)
