@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--cpu-L", type=int, default=2304, help="lattice of the oracle sample")
     ap.add_argument("--ref-L", type=int, default=384, help="lattice of one reference-arm step")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-replicas arm")
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--seq-steps", type=int, default=2,
+                    help="steps per replica of the sequential single-lattice comparison")
     return ap.parse_args()
 
 
@@ -240,7 +244,72 @@ def run_ours(args, rank, world, local):
         ms32 = max_over_ranks(ms32)
         out["fp32"] = dict(ms=ms32, phases=ph32, launches=l32, obs=lat32.observables())
         lat32.close()
+        del lat32
+    if not args.no_batch:
+        out["batch"] = run_batch(args, rank, local)
     return out
+
+
+def run_batch(args, rank, local):
+    """64 replicas (L in {64, 128, 256, 512} x 16 temperatures in [0.2, 1.5] D, seed r,
+    FP32-guarded) advanced together, against the same replicas run one after another as
+    single lattices."""
+    import torch
+    import paper_1503_03295_gb300 as sco
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    ps = sco.replica_params(precision=sco.FP32_GUARDED)
+    for p in ps:
+        p.seed += 1000 * rank
+    ntot = sum(p.Lx * p.Ly for p in ps)
+    b = sco.Batch(ps, stream=stream.cuda_stream)
+    tuning = b.autotune(trial_steps=2)
+    b.run(args.warmup)
+    i0 = b.info()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.run(args.batch_steps)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    i1 = b.info()
+    obs = [b.observables(r) for r in (0, 15, 48, 63)]
+    b.close()
+    del b
+    # the same replicas as single lattices, one after another
+    seq_ms = 0.0
+    seq_launches = 0
+    for p in ps:
+        lat = sco.Lattice(p, stream=stream.cuda_stream)
+        lat.sweep(1)
+        lat.sync()
+        l0 = lat.observables()["kernel_launches"]
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            lat.sweep(args.seq_steps)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        seq_ms += e0.elapsed_time(e1)
+        seq_launches += lat.observables()["kernel_launches"] - l0
+        lat.close()
+    value = ntot * args.batch_steps / (ms / 1e3)
+    seq_value = ntot * args.seq_steps / (seq_ms / 1e3)
+    return {
+        "value": value, "unit": UNIT, "ms_per_step": ms / args.batch_steps,
+        "steps": args.batch_steps, "replicas": len(ps), "sites": ntot, "precision": "fp32_guarded",
+        "workload": "64 replicas: L in {64,128,256,512} x 16, T = (0.2 + b 1.3/15) D, seed r, "
+                    "J=0, D=1, n_sw=1",
+        "tuning": tuning, "gpu_launches": i1["launches"] - i0["launches"],
+        "graph_launches": i1["graph_launches"] - i0["graph_launches"], "replans": i1["replans"],
+        "sample_max_degree": {str(r): o["max_degree"] for r, o in zip((0, 15, 48, 63), obs)},
+        "sequential": {"value": seq_value, "ms_per_step_all_replicas": seq_ms / args.seq_steps,
+                       "steps": args.seq_steps, "gpu_launches": seq_launches},
+        "speedup_vs_sequential": value / seq_value,
+    }
 
 
 def cpu_baseline(L, T, seed):
@@ -324,6 +393,8 @@ def main():
             "roofline_phases": rooflines(p32, N, k, levels, cand, hbm, how, False),
             "guard_hits_fp32": f32["obs"]["guard_hits_fp32"],
             "guard_hits_fp64": f32["obs"]["guard_hits_fp64"]}
+    if "batch" in res:
+        line["batched"] = res["batch"]
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_L, args.T, args.seed)
     print(json.dumps(line), flush=True)

@@ -169,6 +169,68 @@ sco_status sco_kw_colour_static(const uint32_t* row_ptr, const uint32_t* col, in
                                 int32_t variant, uint32_t* colour, int32_t* max_degree,
                                 int32_t* rounds, void* stream);
 
+/* ---- Batched replicas ------------------------------------------------------------------
+ * A batch holds n_replicas independent lattices (any sizes, temperatures, seeds, J, D; one
+ * precision and one n_sw for all) that advance together: each phase of Fig. 1 (switch +
+ * CSR, KW colouring, colour-class sweep) is one launch over every replica, the sweep is one
+ * persistent cooperative kernel per MC step that walks the colours with grid barriers, and
+ * no step needs the host, so runs of steps are replayed as CUDA graphs.  Replica r follows
+ * exactly the trajectory of a single lattice created with p[r] (same decisions, bit-identical
+ * spins), whatever the tuning.
+ *
+ * Sizes that depend on the switched graph (CSR entries, overflow half-edges, palette) are
+ * checked on the device; a step that would overflow is abandoned before any spin changes
+ * and repeated after the host has grown the buffers ("replan"), so results do not depend on
+ * the initial sizes either. */
+typedef struct sco_batch sco_batch;
+
+/* Result-invariant launch choices (autotuned or set by hand). */
+typedef struct {
+  int32_t steps_per_graph;     /* MC steps per replayed CUDA graph, >= 1 */
+  int32_t sweep_blocks_per_sm; /* resident blocks per SM of the persistent sweep, >= 1 */
+  int32_t kw_blocks_per_sm;    /* resident blocks per SM of the KW level kernel, >= 1 */
+  int32_t use_graph;           /* 1: capture and replay graphs; 0: launch directly */
+} sco_batch_tuning;
+
+/* Creates a batch of n_replicas lattices from p[0 .. n_replicas-1] (1 <= n_replicas <= 1024,
+ * total sites < 2^31; every p[r] valid for sco_init; precision and n_sw equal for all).
+ * stream: a cudaStream_t, or NULL for a stream the batch creates and owns (the legacy
+ * default stream cannot be captured into graphs).  Draws every replica's initial spins.
+ * Synchronises. */
+sco_status sco_batch_init(const sco_params* p, int32_t n_replicas, void* stream,
+                          sco_batch** out);
+void sco_batch_destroy(sco_batch* b);
+
+/* n_mcs MC steps of every replica (switch + colour every n_sw steps, then the sweep).
+ * Synchronises once at the end (and once per replan). */
+sco_status sco_batch_run(sco_batch* b, int32_t n_mcs);
+
+/* Times the candidate tunings on real MC steps (trial_steps per candidate and one warm-up;
+ * the steps count as MC steps done, and results do not depend on the tuning), keeps the
+ * fastest and returns it in *chosen (may be NULL). */
+sco_status sco_batch_autotune(sco_batch* b, int32_t trial_steps, sco_batch_tuning* chosen);
+sco_status sco_batch_set_tuning(sco_batch* b, const sco_batch_tuning* t);
+sco_status sco_batch_get_tuning(sco_batch* b, sco_batch_tuning* t);
+
+/* Per-replica access, 0 <= r < n_replicas; same meaning and layouts as the single-lattice
+ * calls (spins SoA 3*N_r doubles, graph with replica-local indices). */
+sco_status sco_batch_observables(sco_batch* b, int32_t r, sco_obs* out, int32_t want_full);
+sco_status sco_batch_get_spins(sco_batch* b, int32_t r, double* xyz, int32_t on_device);
+sco_status sco_batch_set_spins(sco_batch* b, int32_t r, const double* xyz, int32_t on_device);
+sco_status sco_batch_get_sizes(sco_batch* b, int32_t r, int64_t* n_sites, int64_t* n_entries,
+                               int32_t* max_degree, int32_t* palette);
+sco_status sco_batch_get_graph(sco_batch* b, int32_t r, uint32_t* row_ptr, uint32_t* col,
+                               uint32_t* colour);
+sco_status sco_batch_get_accepts(sco_batch* b, int32_t r, uint8_t* acc);
+
+/* Totals: sites, MC steps done, kernel launches enqueued, graph replays, replans.  Any
+ * pointer may be NULL. */
+sco_status sco_batch_info(sco_batch* b, int64_t* total_sites, int64_t* steps_done,
+                          int64_t* launches, int64_t* graph_launches, int32_t* replans);
+
+/* Waits for the batch's stream; returns the sticky device status. */
+sco_status sco_batch_sync(sco_batch* b);
+
 /* Waits for the context's stream; returns the sticky device status. */
 sco_status sco_sync(sco_ctx* c);
 

@@ -32,6 +32,14 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("colour_variant", C.c_int32), ("replica", C.c_int32)]
 
 
+class BatchTuning(C.Structure):
+    _fields_ = [("steps_per_graph", C.c_int32), ("sweep_blocks_per_sm", C.c_int32),
+                ("kw_blocks_per_sm", C.c_int32), ("use_graph", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Obs(C.Structure):
     _fields_ = [("e_switched", C.c_double), ("e_exchange", C.c_double), ("e_full", C.c_double),
                 ("mx", C.c_double), ("my", C.c_double), ("mz", C.c_double),
@@ -81,6 +89,22 @@ def load():
         "sco_kw_colour_static": ([vp, vp, C.c_int64, C.c_int32, vp, C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], st),
         "sco_strerror": ([C.c_int], C.c_char_p),
+        "sco_batch_init": ([vp, C.c_int32, vp, C.POINTER(vp)], st),
+        "sco_batch_destroy": ([vp], None),
+        "sco_batch_run": ([vp, C.c_int32], st),
+        "sco_batch_autotune": ([vp, C.c_int32, C.POINTER(BatchTuning)], st),
+        "sco_batch_set_tuning": ([vp, C.POINTER(BatchTuning)], st),
+        "sco_batch_get_tuning": ([vp, C.POINTER(BatchTuning)], st),
+        "sco_batch_observables": ([vp, C.c_int32, C.POINTER(Obs), C.c_int32], st),
+        "sco_batch_get_spins": ([vp, C.c_int32, vp, C.c_int32], st),
+        "sco_batch_set_spins": ([vp, C.c_int32, vp, C.c_int32], st),
+        "sco_batch_get_sizes": ([vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)], st),
+        "sco_batch_get_graph": ([vp, C.c_int32, vp, vp, vp], st),
+        "sco_batch_get_accepts": ([vp, C.c_int32, vp], st),
+        "sco_batch_info": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                            C.POINTER(C.c_int64), C.POINTER(C.c_int32)], st),
+        "sco_batch_sync": ([vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -257,3 +281,132 @@ class Lattice:
         _check(load().sco_get_timing(self._h, _ptr(ms), _ptr(calls)), "sco_get_timing")
         return dict(switch_ms=ms[0], colour_ms=ms[1], sweep_ms=ms[2], switch_calls=int(calls[0]),
                     colour_calls=int(calls[1]), sweep_calls=int(calls[2]))
+
+
+class Batch:
+    """Replicas that advance together (a thin handle on ``sco_batch``): one launch per phase
+    over all replicas, runs of steps replayed as CUDA graphs.  ``params`` is a list of
+    :class:`Params` (one precision and one n_sw for all).  ``stream`` None lets the batch
+    own a stream."""
+
+    def __init__(self, params, stream=None):
+        self.params = list(params)
+        arr = (Params * len(self.params))(*self.params)
+        h = C.c_void_p()
+        _check(load().sco_batch_init(arr, len(self.params), C.c_void_p(stream or 0), C.byref(h)),
+               "sco_batch_init")
+        self._h = h
+        self.N = [p.Lx * p.Ly for p in self.params]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sco_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __len__(self):
+        return len(self.params)
+
+    def run(self, n=1):
+        _check(load().sco_batch_run(self._h, int(n)), "sco_batch_run")
+
+    def sync(self):
+        _check(load().sco_batch_sync(self._h), "sco_batch_sync")
+
+    def autotune(self, trial_steps=2):
+        t = BatchTuning()
+        _check(load().sco_batch_autotune(self._h, int(trial_steps), C.byref(t)),
+               "sco_batch_autotune")
+        return t.as_dict()
+
+    def set_tuning(self, steps_per_graph=4, sweep_blocks_per_sm=1, kw_blocks_per_sm=1,
+                   use_graph=1):
+        t = BatchTuning(steps_per_graph, sweep_blocks_per_sm, kw_blocks_per_sm, use_graph)
+        _check(load().sco_batch_set_tuning(self._h, C.byref(t)), "sco_batch_set_tuning")
+
+    def tuning(self):
+        t = BatchTuning()
+        _check(load().sco_batch_get_tuning(self._h, C.byref(t)), "sco_batch_get_tuning")
+        return t.as_dict()
+
+    def info(self):
+        a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        e = C.c_int32()
+        _check(load().sco_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d),
+                                     C.byref(e)), "sco_batch_info")
+        return dict(total_sites=a.value, steps_done=b.value, launches=c.value,
+                    graph_launches=d.value, replans=e.value)
+
+    def observables(self, r, full=False):
+        o = Obs()
+        _check(load().sco_batch_observables(self._h, int(r), C.byref(o), int(bool(full))),
+               "sco_batch_observables")
+        return o.as_dict()
+
+    def spins(self, r):
+        a = np.empty(3 * self.N[r])
+        _check(load().sco_batch_get_spins(self._h, int(r), _ptr(a), 0), "sco_batch_get_spins")
+        return a
+
+    def set_spins(self, r, xyz):
+        a = np.ascontiguousarray(xyz, np.float64)
+        if a.size != 3 * self.N[r]:
+            raise ValueError("expected %d values" % (3 * self.N[r]))
+        _check(load().sco_batch_set_spins(self._h, int(r), _ptr(a), 0), "sco_batch_set_spins")
+
+    def get_spins_device(self, r, dev_ptr):
+        _check(load().sco_batch_get_spins(self._h, int(r), C.c_void_p(dev_ptr), 1),
+               "sco_batch_get_spins")
+
+    def set_spins_device(self, r, dev_ptr):
+        _check(load().sco_batch_set_spins(self._h, int(r), C.c_void_p(dev_ptr), 1),
+               "sco_batch_set_spins")
+
+    def sizes(self, r):
+        n, e, d, g = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
+        _check(load().sco_batch_get_sizes(self._h, int(r), C.byref(n), C.byref(e), C.byref(d),
+                                          C.byref(g)), "sco_batch_get_sizes")
+        return n.value, e.value, d.value, g.value
+
+    def graph(self, r):
+        _, nnz, _, _ = self.sizes(r)
+        rp = np.empty(self.N[r] + 1, np.uint32)
+        col = np.empty(max(nnz, 1), np.uint32)
+        _check(load().sco_batch_get_graph(self._h, int(r), _ptr(rp), _ptr(col), None),
+               "sco_batch_get_graph")
+        return rp, col[:nnz]
+
+    def colours(self, r):
+        c = np.empty(self.N[r], np.uint32)
+        _check(load().sco_batch_get_graph(self._h, int(r), None, None, _ptr(c)),
+               "sco_batch_get_graph")
+        return c
+
+    def accepts(self, r):
+        a = np.empty(self.N[r], np.uint8)
+        _check(load().sco_batch_get_accepts(self._h, int(r), _ptr(a)), "sco_batch_get_accepts")
+        return a
+
+
+def replica_params(L_list=(64, 128, 256, 512), n_T=16, T_lo=0.2, T_hi=1.5,
+                   precision=FP32_GUARDED, **kw):
+    """Replica r = n_T a + b: L = L_list[a], T = (T_lo + b (T_hi - T_lo) / (n_T - 1)) D,
+    seed r (the batched workload: 4 sizes x 16 temperatures)."""
+    out = []
+    for a, L in enumerate(L_list):
+        for b in range(n_T):
+            r = n_T * a + b
+            T = T_lo + b * (T_hi - T_lo) / (n_T - 1) if n_T > 1 else T_lo
+            out.append(make_params(L, T=T, seed=r, precision=precision, **kw))
+    return out

@@ -8,6 +8,7 @@
 
 #include "sco.h"
 #include "sco_internal.h"
+#include "batch.h"
 
 namespace sco {
 
@@ -32,6 +33,40 @@ static dd ln2_dd() {
     pw = dd_mul(pw, x2);
   }
   return dd_ldexp(sum, 1);
+}
+
+bool params_ok(const sco_params* p) {
+  if (!p) return false;
+  if (p->Lx < 1 || p->Ly < 1 || p->Lx > 32767 || p->Ly > 32767) return false;
+  if ((int64_t)p->Lx * p->Ly >= (1ll << 30)) return false;
+  if (!(p->T > 0.0) || !std::isfinite(p->T) || !(p->D >= 0.0) || !std::isfinite(p->D) ||
+      !std::isfinite(p->J))
+    return false;
+  if (p->n_sw < 1 || p->precision < 0 || p->precision > 1) return false;
+  if (p->colour_variant < 0 || p->colour_variant > 1) return false;
+  return true;
+}
+
+
+DevParams make_dev_params(const sco_params& p) {
+  DevParams P{};
+  P.Lx = p.Lx;
+  P.Ly = p.Ly;
+  P.N = (int64_t)p.Lx * p.Ly;
+  P.K = (int64_t)(p.Lx - 1) + (int64_t)(p.Ly - 1) * (2 * (int64_t)p.Lx - 1);
+  P.J = p.J;
+  P.D = p.D;
+  P.beta = 1.0 / p.T;
+  P.bD = P.beta * p.D;
+  P.inv_bD58 = P.bD > 0.0 ? 0x1p58 / P.bD : 0.0;
+  P.inv_bD58_f = (float)P.inv_bD58;
+  P.lx_magic = div_magic((unsigned long long)p.Lx);
+  P.key0 = p.seed;
+  P.key1 = (uint64_t)(uint32_t)p.replica;
+  const dd l2 = ln2_dd();
+  P.ln2_hi = l2.hi;
+  P.ln2_lo = l2.lo;
+  return P;
 }
 
 }  // namespace sco
@@ -166,6 +201,25 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float*
   SCO_TRY(csr_scan(c->P, c->sw, c->row_ptr, c->cnt, c->st, &c->launches));
   sco_status st = read_counters(c);
   if (st != SCO_OK) return st;
+  if (c->hcnt->ovf_n > c->sw.ovf_cap) {
+    // more half-edges beyond the per-site slots than the overflow list holds: grow it and
+    // switch again (the switch is a pure function of the spins and the epoch)
+    const unsigned long long need = c->hcnt->ovf_n + c->hcnt->ovf_n / 4 + 1024;
+    if (need > 0x7FFFFFFFull) return SCO_ECAPACITY;
+    cudaFree(c->sw.ovf);
+    c->sw.ovf = nullptr;
+    SCO_TRY(cudaMalloc(&c->sw.ovf, 2 * need * sizeof(uint32_t)));
+    c->sw.ovf_cap = (uint32_t)need;
+    SCO_TRY(cudaMemsetAsync(c->cnt, 0, 4 * sizeof(unsigned long long), c->st));
+    SCO_TRY(cudaMemsetAsync(&c->cnt->max_degree, 0, 2 * sizeof(unsigned), c->st));
+    SCO_TRY(cudaMemsetAsync(&c->cnt->ovf_full, 0, sizeof(int), c->st));
+    SCO_TRY(switch_run(c->P, c->tab, src, src32, c->p.precision, epoch, c->sw, c->cnt, c->st,
+                       &c->launches));
+    SCO_TRY(csr_scan(c->P, c->sw, c->row_ptr, c->cnt, c->st, &c->launches));
+    st = read_counters(c);
+    if (st != SCO_OK) return st;
+    if (c->hcnt->ovf_n > c->sw.ovf_cap) return SCO_ECAPACITY;
+  }
   c->nnz = c->hcnt->nnz;
   SCO_TRY(grow(c->col, c->col_cap, c->nnz > 0 ? c->nnz : 1));
   SCO_TRY(csr_fill(c->P, c->sw, c->row_ptr, c->col, c->hcnt->ovf_n > 0, c->cnt, c->st,
@@ -250,18 +304,6 @@ void free_all(sco_ctx* c) {
   for (auto e : c->pool) cudaEventDestroy(e);
 }
 
-bool params_ok(const sco_params* p) {
-  if (!p) return false;
-  if (p->Lx < 1 || p->Ly < 1 || p->Lx > 32767 || p->Ly > 32767) return false;
-  if ((int64_t)p->Lx * p->Ly >= (1ll << 30)) return false;
-  if (!(p->T > 0.0) || !std::isfinite(p->T) || !(p->D >= 0.0) || !std::isfinite(p->D) ||
-      !std::isfinite(p->J))
-    return false;
-  if (p->n_sw < 1 || p->precision < 0 || p->precision > 1) return false;
-  if (p->colour_variant < 0 || p->colour_variant > 1) return false;
-  return true;
-}
-
 }  // namespace
 
 extern "C" {
@@ -290,23 +332,8 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (!c) return SCO_ENOMEM;
   c->p = *p;
   c->st = (cudaStream_t)stream;
-  DevParams& P = c->P;
-  P.Lx = p->Lx;
-  P.Ly = p->Ly;
-  P.N = (int64_t)p->Lx * p->Ly;
-  P.K = (int64_t)(p->Lx - 1) + (int64_t)(p->Ly - 1) * (2 * (int64_t)p->Lx - 1);
-  P.J = p->J;
-  P.D = p->D;
-  P.beta = 1.0 / p->T;
-  P.bD = P.beta * p->D;
-  P.inv_bD58 = P.bD > 0.0 ? 0x1p58 / P.bD : 0.0;
-  P.inv_bD58_f = (float)P.inv_bD58;
-  P.lx_magic = div_magic((unsigned long long)p->Lx);
-  P.key0 = p->seed;
-  P.key1 = (uint64_t)(uint32_t)p->replica;
-  const dd l2 = ln2_dd();
-  P.ln2_hi = l2.hi;
-  P.ln2_lo = l2.lo;
+  c->P = make_dev_params(*p);
+  const DevParams& P = c->P;
   const int64_t N = P.N;
   auto fail = [&](sco_status s) {
     free_all(c);

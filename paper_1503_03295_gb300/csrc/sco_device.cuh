@@ -42,6 +42,13 @@ __device__ __forceinline__ uint32_t site_row(uint32_t i, const DevParams& P) {
   return div_by_magic(i, P.lx_magic);
 }
 
+// Warp sum (lane 0 receives the total).
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // ---------------------------------------------------------------------------------------
 // Philox4x64-10, Salmon, Moraes, Dror and Shaw (SC'11): two 64x64->128 multiplies per round
 // on counter words 0 and 2, high halves mixed with words 1, 3 and the key, key bumped by

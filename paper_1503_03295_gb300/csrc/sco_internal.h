@@ -25,7 +25,7 @@ struct DevCounters {
   unsigned int kw_rounds;           // t_R (sum over levels of the deepest dependency chain)
   unsigned int n_colours;           // non-empty classes
   int status;                       // sticky device error (sco_status value), 0 if none
-  int pad;
+  int ovf_full;                     // the switch wrote more half-edges than the overflow list holds
   double acc[8];                    // observable accumulators
   unsigned int lev_rounds[32];      // deepest dependency chain per KW level
 };
@@ -50,7 +50,12 @@ struct Table {
   int32_t m_nn[2] = {-1, -1};
 };
 cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches);
+// the two halves: the temperature-dependent tables by (|dx|, |dy|), and the sorted list
+// with its hazard prefix (depends on Lx, Ly only; synchronises)
+cudaError_t table_build_xy(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches);
+cudaError_t table_build_list(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches);
 void table_free(Table& t);
+void table_free_xy(Table& t);
 
 // ---- init / observables (spins.cu) ----
 cudaError_t spins_init(const DevParams& P, double* s, float* s32, cudaStream_t st,

@@ -1,251 +1,14 @@
-// sweep.cu -- step (B) of Sec. 2.1 / step (3) of Fig. 1: Metropolis updates of all sites of
-// one colour class at a time under the switched Hamiltonian H' of Eq. (4).
-//
-// Proposal for site i at MC step t: Philox tag PROPOSE, counter (i, t, a); attempt a uses
-// words 0, 1 for Marsaglia's sphere point and word 2 of the successful attempt is the
-// acceptance uniform u; 64 failed attempts keep the spin.  The move is accepted iff
-// u < exp(-beta dE'), i.e. u == 0 or ln u + beta dE' < 0, with
-//   beta dE' = sum_{surviving j} [beta V(S', S_j) - L(S') - beta V(S, S_j) + L(S)]
-//              - beta J (S' - S) . sum_{nn j} S_j,
-//   L = log(1 - exp(beta (V - Vmax)))   (so that beta Vbar = beta V - L, Eq. (3)).
-// The decision is taken in FP64 (or FP32 in the FP32-guarded form) with a bound on the
-// rounding error of the margin; a site whose margin is inside the bound is settled
-// afterwards by one warp, in FP64 (after FP32) and then in double-double.  Sites of one
-// colour share no pair, so they update independently.
+// sweep.cu -- step (B) of Sec. 2.1 / step (3) of Fig. 1 for one lattice: Metropolis
+// updates of all sites of one colour class at a time (one launch per colour), with the
+// undecided sites settled afterwards by one warp each.  Sites of one colour share no pair,
+// so they update independently.  The per-site decision is in sweep_dev.cuh.
 #include <cstdint>
 
-#include "sco_internal.h"
+#include "sweep_dev.cuh"
 
 namespace sco {
 
 namespace {
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-struct SiteCtx {
-  int64_t i;
-  int32_t xi, yi;
-  double S[3], Sn[3];
-  double u;
-};
-
-// The pseudointeraction terms enter as sum_j [L_o,j - L_n,j] = log(prod z_o) - log(prod z_n)
-// with z = 1 - e^x = -expm1(x): one expm1 per pair energy and two logarithms per site.  The
-// products are renormalised by 2^kScale (exact) so that they never underflow.
-constexpr int kScale64 = 600;
-constexpr int kScale32 = 60;
-
-// Pair field on site i from the sweep table entry {A1, A3, beta Vmax, c0}:
-// f = A1 S_j - A3 (S_j.d) d, V(S) = S.f, x = beta V - beta Vmax.
-//
-// Error bound of the margin mu = ln u + beta dE' (first order, doubled):
-//   per pair, |dx| <= c0 + eps_r |x| (c0 from the table covers |dV| and fl(beta Vmax));
-//   z = -expm1(x) has relative error eps_f + |dx| / z;  log of a product of n factors adds
-//   n eps_r;  log itself eps_f |log P|;  beta sum (V' - V) adds 2 sum c0 + (n + 2) eps_r |.|.
-// With zmin = min z and xmax = max |x|, sum_j |dx_j| / z_j <= (sum c0 + n eps_r xmax) / zmin,
-// which must stay below 2^-10 (first order) or the decision is left undecided.
-
-// FP64 decision (0: reject, 1: accept, 2: undecided).  eps_r = 2^-52 (unit roundoff, with
-// margin), eps_f = 2^-50 (expm1 / log within 4 ulp).
-__device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
-                                           const double4_32a* __restrict__ sw,
-                                           const double* __restrict__ s,
-                                           const uint32_t* __restrict__ row_ptr,
-                                           const uint32_t* __restrict__ col) {
-  const double beta = P.beta;
-  const double S0 = c.S[0], S1 = c.S[1], S2 = c.S[2];
-  const double N0 = c.Sn[0], N1 = c.Sn[1], N2 = c.Sn[2];
-  double sdv = 0.0, sdv_abs = 0.0, pz_o = 1.0, pz_n = 1.0, zmin = 1.0, xmax = 0.0, c0s = 0.0;
-  int sc_o = 0, sc_n = 0, n = 0;
-  const uint32_t e1 = row_ptr[c.i + 1];
-  for (uint32_t e = row_ptr[c.i]; e < e1; ++e) {
-    const uint32_t cj = col[e];
-    if (cj & kExchOnly) continue;
-    const int64_t j = cj;
-    const uint32_t yj = site_row((uint32_t)j, P);
-    const int32_t dx = (int32_t)((uint32_t)j - yj * (uint32_t)P.Lx) - c.xi;
-    const int32_t dy = (int32_t)yj - c.yi;
-    const double4_32a t = sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
-    const double fx = (double)dx, fy = (double)dy;
-    const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
-    const double tp = t.y * (bx * fx + by * fy);
-    const double gx = t.x * bx - tp * fx;
-    const double gy = t.x * by - tp * fy;
-    const double gz = t.x * bz;
-    const double Vn = N0 * gx + N1 * gy + N2 * gz;
-    const double Vo = S0 * gx + S1 * gy + S2 * gz;
-    const double xn = beta * Vn - t.z, xo = beta * Vo - t.z;
-    if (!(xn < 0.0) || !(xo < 0.0)) return 2;
-    const double zn = -expm1(xn), zo = -expm1(xo);
-    pz_n *= zn;
-    pz_o *= zo;
-    if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
-    if (pz_o < 0x1p-600) { pz_o *= 0x1p600; ++sc_o; }
-    const double dv = Vn - Vo;
-    sdv += dv;
-    sdv_abs += fabs(dv);
-    zmin = fmin(zmin, fmin(zn, zo));
-    xmax = fmax(xmax, fmax(-xn, -xo));
-    c0s += t.w;
-    ++n;
-  }
-  const double lin = n > 0 ? (c0s + n * 0x1p-52 * xmax) / zmin : 0.0;
-  if (!(lin <= 0x1p-10)) return 2;
-  double tex = 0.0, bex = 0.0;
-  if (P.J != 0.0) {
-    double h0 = 0.0, h1 = 0.0, h2 = 0.0;
-    const int64_t nb[4] = {c.xi > 0 ? c.i - 1 : -1, c.xi + 1 < P.Lx ? c.i + 1 : -1,
-                           c.yi > 0 ? c.i - P.Lx : -1, c.yi + 1 < P.Ly ? c.i + P.Lx : -1};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (nb[q] < 0) continue;
-      h0 += s[nb[q]];
-      h1 += s[P.N + nb[q]];
-      h2 += s[2 * P.N + nb[q]];
-    }
-    const double dot = (c.Sn[0] - c.S[0]) * h0 + (c.Sn[1] - c.S[1]) * h1 + (c.Sn[2] - c.S[2]) * h2;
-    tex = -(beta * P.J) * dot;
-    bex = 0x1p-44 * fabs(beta * P.J);
-  }
-  const double lo = log(pz_o), ln = log(pz_n);
-  // prod z = stored product * 2^(-kScale * count)
-  const double scale = (double)((sc_n - sc_o) * kScale64) * P.ln2_hi;
-  const double lu = log(c.u);
-  const double bdv = beta * sdv;
-  const double mu = lu + ((bdv + tex) + ((lo - ln) + scale));
-  const double B = 2.0 * (2.0 * c0s + (double)(n + 2) * 0x1p-52 * beta * sdv_abs + 2.0 * lin +
-                          n * (0x1p-48 + 0x1p-51) + 0x1p-50 * (fabs(lo) + fabs(ln) + fabs(lu)) +
-                          bex + 0x1p-51 * (fabs(scale) + fabs(tex) + fabs(bdv) + fabs(mu)));
-  if (mu < -B) return 1;
-  if (mu > B) return 0;
-  return 2;
-}
-
-// FP32 screen of the same decision: shadow spins (|dS| <= 2^-24 per component), FP32 table
-// constants, CUDA's single-precision expm1f / logf (<= 1 ulp; 4x margin: eps_f = 2^-21),
-// eps_r = 2^-23, and a compensated (Neumaier) sum of the V' - V terms.
-__device__ __forceinline__ int accept_fp32(const DevParams& P, const SiteCtx& c,
-                                           const float4* __restrict__ sw,
-                                           const float* __restrict__ s32,
-                                           const uint32_t* __restrict__ row_ptr,
-                                           const uint32_t* __restrict__ col) {
-  if (c.u < 0x1p-100) return 2;
-  const float beta = (float)P.beta;
-  const float ax = (float)c.S[0], ay = (float)c.S[1], az = (float)c.S[2];
-  const float nx = (float)c.Sn[0], ny = (float)c.Sn[1], nz = (float)c.Sn[2];
-  float sum = 0.f, comp = 0.f, sum_abs = 0.f, pz_o = 1.f, pz_n = 1.f, lin = 0.f, c0s = 0.f;
-  int sc_o = 0, sc_n = 0, n = 0;
-  const uint32_t e1 = row_ptr[c.i + 1];
-  for (uint32_t e = row_ptr[c.i]; e < e1; ++e) {
-    const uint32_t cj = col[e];
-    if (cj & kExchOnly) continue;
-    const int64_t j = cj;
-    const uint32_t yj = site_row((uint32_t)j, P);
-    const int32_t dx = (int32_t)((uint32_t)j - yj * (uint32_t)P.Lx) - c.xi;
-    const int32_t dy = (int32_t)yj - c.yi;
-    const float4 t =
-        __ldg(&sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)]);
-    const float bx = s32[j], by = s32[P.N + j], bz = s32[2 * P.N + j];
-    const float fx = (float)dx, fy = (float)dy;
-    const float tp = t.y * (bx * fx + by * fy);
-    const float gx = t.x * bx - tp * fx;
-    const float gy = t.x * by - tp * fy;
-    const float gz = t.x * bz;
-    const float Vn = nx * gx + ny * gy + nz * gz;
-    const float Vo = ax * gx + ay * gy + az * gz;
-    const float xn = beta * Vn - t.z, xo = beta * Vo - t.z;
-    if (!(xn < 0.f) || !(xo < 0.f)) return 2;
-    const float zn = -expm1f(xn), zo = -expm1f(xo);
-    if (!(zn >= 0x1p-60f) || !(zo >= 0x1p-60f)) return 2;
-    // |dx| / z per pair (first order needs it small); FP32 reciprocal, 1.001 for its rounding
-    const float ln_ = (t.w + 0x1p-23f * -xn) * (1.001f * __frcp_rn(zn));
-    const float lo_ = (t.w + 0x1p-23f * -xo) * (1.001f * __frcp_rn(zo));
-    if (!(ln_ <= 0x1p-10f) || !(lo_ <= 0x1p-10f)) return 2;
-    lin += ln_ + lo_;
-    pz_n *= zn;
-    pz_o *= zo;
-    if (pz_n < 0x1p-60f) { pz_n *= 0x1p60f; ++sc_n; }
-    if (pz_o < 0x1p-60f) { pz_o *= 0x1p60f; ++sc_o; }
-    const float dv = Vn - Vo;
-    const float tsum = sum + dv;  // Neumaier compensated summation
-    comp += fabsf(sum) >= fabsf(dv) ? (sum - tsum) + dv : (dv - tsum) + sum;
-    sum = tsum;
-    sum_abs += fabsf(dv);
-    c0s += t.w;
-    ++n;
-  }
-  float tex = 0.f, bex = 0.f;
-  if (P.J != 0.0) {
-    float h0 = 0.f, h1 = 0.f, h2 = 0.f;
-    const int64_t nb[4] = {c.xi > 0 ? c.i - 1 : -1, c.xi + 1 < P.Lx ? c.i + 1 : -1,
-                           c.yi > 0 ? c.i - P.Lx : -1, c.yi + 1 < P.Ly ? c.i + P.Lx : -1};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (nb[q] < 0) continue;
-      h0 += s32[nb[q]];
-      h1 += s32[P.N + nb[q]];
-      h2 += s32[2 * P.N + nb[q]];
-    }
-    const float bj = (float)(P.beta * P.J);
-    tex = -bj * ((nx - ax) * h0 + (ny - ay) * h1 + (nz - az) * h2);
-    bex = 0x1p-14f * fabsf(bj);
-  }
-  const float lo = logf(pz_o), ln = logf(pz_n);
-  const float scale = (float)((sc_n - sc_o) * kScale32) * 0.693147182f;
-  const float lu = logf((float)c.u);
-  const float bdv = beta * (sum + comp);
-  const float mu = lu + ((bdv + tex) + ((lo - ln) + scale));
-  const float B = 2.0f * (2.0f * c0s * 1.001f + (float)(n + 2) * 0x1p-23f * beta * sum_abs +
-                          lin * 1.001f + n * (0x1p-19f + 0x1p-22f) +
-                          0x1p-21f * (fabsf(lo) + fabsf(ln)) + 0x1p-20f * fabsf(lu) + 0x1p-23f +
-                          bex + 0x1p-21f * (fabsf(scale) + fabsf(tex) + fabsf(bdv) + fabsf(mu)));
-  if (mu < -B) return 1;
-  if (mu > B) return 0;
-  return 2;
-}
-
-// Proposal of site i at MC step t (Philox tag PROPOSE, counter (i, t, a)); false if all 64
-// attempts were rejected.
-__device__ __forceinline__ bool propose(const DevParams& P, SiteCtx& c, uint64_t step) {
-  for (uint64_t a = 0; a < 64; ++a) {
-    const W4 w = philox((uint64_t)c.i, step, a, kTagPropose, P.key0, P.key1);
-    if (marsaglia(w.w[0], w.w[1], c.Sn[0], c.Sn[1], c.Sn[2])) {
-      c.u = u53(w.w[2]);
-      return true;
-    }
-  }
-  return false;
-}
-
-__device__ __forceinline__ void load_site(const DevParams& P, SiteCtx& c, uint32_t i,
-                                          const double* __restrict__ s) {
-  c.i = i;
-  c.yi = (int32_t)site_row(i, P);
-  c.xi = (int32_t)(i - (uint32_t)c.yi * (uint32_t)P.Lx);
-  c.S[0] = s[i];
-  c.S[1] = s[P.N + i];
-  c.S[2] = s[2 * P.N + i];
-}
-
-__device__ __forceinline__ void write_site(const DevParams& P, const SiteCtx& c, bool ok,
-                                           double* __restrict__ s, float* __restrict__ s32,
-                                           uint8_t* __restrict__ acc) {
-  if (ok) {
-    s[c.i] = c.Sn[0];
-    s[P.N + c.i] = c.Sn[1];
-    s[2 * P.N + c.i] = c.Sn[2];
-    if (s32) {
-      s32[c.i] = (float)c.Sn[0];
-      s32[P.N + c.i] = (float)c.Sn[1];
-      s32[2 * P.N + c.i] = (float)c.Sn[2];
-    }
-  }
-  acc[c.i] = ok ? 1 : 0;
-}
 
 // One thread per site of the class.  A site whose decision stays inside the error bound is
 // appended to the deferred list of the colour and settled by k_resolve (one warp per site),
@@ -289,167 +52,6 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) k_sweep(const DevParam
     if (PREC == 1) atomicAdd(&cnt->guard_fp32, nd);
     else atomicAdd(&cnt->guard_fp64, nd);
   }
-}
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ double warp_min_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ dd warp_sum_dd(dd v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const dd w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-    v = dd_add(v, w);
-  }
-  return v;
-}
-
-// The FP64 decision of accept_fp64 with the pairs of the site spread over the 32 lanes of a
-// warp (partial sums, products taken to logarithms per lane, then reduced).  Same bound.
-__device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
-                                const double4_32a* __restrict__ sw,
-                                const double* __restrict__ s,
-                                const uint32_t* __restrict__ row_ptr,
-                                const uint32_t* __restrict__ col, int lane) {
-  const double beta = P.beta;
-  double sdv = 0.0, sdv_abs = 0.0, pz_o = 1.0, pz_n = 1.0, zmin = 1.0, xmax = 0.0, c0s = 0.0;
-  int sc_o = 0, sc_n = 0, n = 0, bad = 0;
-  const uint32_t e1 = row_ptr[c.i + 1];
-  for (uint32_t e = row_ptr[c.i] + lane; e < e1; e += 32) {
-    const uint32_t cj = col[e];
-    if (cj & kExchOnly) continue;
-    const uint32_t j = cj;
-    const uint32_t yj = site_row(j, P);
-    const int32_t dx = (int32_t)(j - yj * (uint32_t)P.Lx) - c.xi;
-    const int32_t dy = (int32_t)yj - c.yi;
-    const double4_32a t = sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
-    const double fx = (double)dx, fy = (double)dy;
-    const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
-    const double tp = t.y * (bx * fx + by * fy);
-    const double gx = t.x * bx - tp * fx;
-    const double gy = t.x * by - tp * fy;
-    const double gz = t.x * bz;
-    const double Vn = c.Sn[0] * gx + c.Sn[1] * gy + c.Sn[2] * gz;
-    const double Vo = c.S[0] * gx + c.S[1] * gy + c.S[2] * gz;
-    const double xn = beta * Vn - t.z, xo = beta * Vo - t.z;
-    if (!(xn < 0.0) || !(xo < 0.0)) {
-      bad = 1;
-      continue;
-    }
-    const double zn = -expm1(xn), zo = -expm1(xo);
-    pz_n *= zn;
-    pz_o *= zo;
-    if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
-    if (pz_o < 0x1p-600) { pz_o *= 0x1p600; ++sc_o; }
-    const double dv = Vn - Vo;
-    sdv += dv;
-    sdv_abs += fabs(dv);
-    zmin = fmin(zmin, fmin(zn, zo));
-    xmax = fmax(xmax, fmax(-xn, -xo));
-    c0s += t.w;
-    ++n;
-  }
-  // per lane: log of its products, with the renormalisation folded in
-  const double lo = log(pz_o) - (double)(sc_o * kScale64) * P.ln2_hi;
-  const double ln = log(pz_n) - (double)(sc_n * kScale64) * P.ln2_hi;
-  const double lsum = warp_sum_d(lo - ln);
-  const double labs = warp_sum_d(fabs(lo) + fabs(ln));
-  sdv = warp_sum_d(sdv);
-  sdv_abs = warp_sum_d(sdv_abs);
-  c0s = warp_sum_d(c0s);
-  zmin = warp_min_d(zmin);
-  xmax = warp_max_d(xmax);
-  n = __reduce_add_sync(0xffffffffu, n);
-  bad = __reduce_or_sync(0xffffffffu, bad);
-  if (bad) return 2;
-  const double lin = n > 0 ? (c0s + n * 0x1p-52 * xmax) / zmin : 0.0;
-  if (!(lin <= 0x1p-10)) return 2;
-  double tex = 0.0, bex = 0.0;
-  if (P.J != 0.0) {
-    double h0 = 0.0, h1 = 0.0, h2 = 0.0;
-    const int64_t nb[4] = {c.xi > 0 ? c.i - 1 : -1, c.xi + 1 < P.Lx ? c.i + 1 : -1,
-                           c.yi > 0 ? c.i - P.Lx : -1, c.yi + 1 < P.Ly ? c.i + P.Lx : -1};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (nb[q] < 0) continue;
-      h0 += s[nb[q]];
-      h1 += s[P.N + nb[q]];
-      h2 += s[2 * P.N + nb[q]];
-    }
-    const double dot = (c.Sn[0] - c.S[0]) * h0 + (c.Sn[1] - c.S[1]) * h1 + (c.Sn[2] - c.S[2]) * h2;
-    tex = -(beta * P.J) * dot;
-    bex = 0x1p-44 * fabs(beta * P.J);
-  }
-  const double lu = log(c.u);
-  const double bdv = beta * sdv;
-  const double mu = lu + ((bdv + tex) + lsum);
-  const double B = 2.0 * (2.0 * c0s + (double)(n + 2) * 0x1p-52 * beta * sdv_abs + 2.0 * lin +
-                          n * (0x1p-48 + 0x1p-51) + 0x1p-50 * (labs + fabs(lu)) + 0x1p-49 * labs +
-                          bex + 0x1p-51 * (fabs(tex) + fabs(bdv) + fabs(mu)));
-  if (mu < -B) return 1;
-  if (mu > B) return 0;
-  return 2;
-}
-
-// The same comparison in double-double, pairs spread over the lanes.
-__device__ bool accept_dd_warp(const DevParams& P, const SiteCtx& c,
-                               const double* __restrict__ s,
-                               const uint32_t* __restrict__ row_ptr,
-                               const uint32_t* __restrict__ col, int lane) {
-  const dd ln2 = {P.ln2_hi, P.ln2_lo};
-  dd sum = dd_from(0.0);
-  int inf = 0;
-  const uint32_t e1 = row_ptr[c.i + 1];
-  for (uint32_t e = row_ptr[c.i] + lane; e < e1; e += 32) {
-    const uint32_t cj = col[e];
-    if (cj & kExchOnly) continue;
-    const uint32_t j = cj;
-    const uint32_t yj = site_row(j, P);
-    const int32_t dx = (int32_t)(j - yj * (uint32_t)P.Lx) - c.xi;
-    const int32_t dy = (int32_t)yj - c.yi;
-    const int64_t r2 = (int64_t)dx * dx + (int64_t)dy * dy;
-    const double cc = coupling_c(r2);
-    const dd Vm = dd_vmax(P.D, hazard_A(r2));
-    const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-    const dd Vn = dd_pair_V(P.D, cc, (double)r2, c.Sn, Sj, (double)dx, (double)dy);
-    const dd Vo = dd_pair_V(P.D, cc, (double)r2, c.S, Sj, (double)dx, (double)dy);
-    const dd xn = dd_mul_d(dd_sub(Vn, Vm), P.beta);
-    const dd xo = dd_mul_d(dd_sub(Vo, Vm), P.beta);
-    if (!(xn.hi < 0.0)) {  // Vbar(S') = +inf
-      inf = 1;
-      continue;
-    }
-    sum = dd_add(sum, dd_mul_d(dd_sub(Vn, Vo), P.beta));
-    sum = dd_sub(sum, dd_log1mexp(xn, ln2));
-    sum = dd_add(sum, dd_log1mexp(xo, ln2));
-  }
-  sum = warp_sum_dd(sum);
-  if (__reduce_or_sync(0xffffffffu, inf)) return false;
-  if (P.J != 0.0) {
-    dd h[3] = {dd_from(0.0), dd_from(0.0), dd_from(0.0)};
-    const int64_t nb[4] = {c.xi > 0 ? c.i - 1 : -1, c.xi + 1 < P.Lx ? c.i + 1 : -1,
-                           c.yi > 0 ? c.i - P.Lx : -1, c.yi + 1 < P.Ly ? c.i + P.Lx : -1};
-    for (int q = 0; q < 4; ++q) {
-      if (nb[q] < 0) continue;
-      for (int a = 0; a < 3; ++a) h[a] = dd_add(h[a], dd_from(s[a * P.N + nb[q]]));
-    }
-    dd dot = dd_from(0.0);
-    for (int a = 0; a < 3; ++a) dot = dd_add(dot, dd_mul(two_sum(c.Sn[a], -c.S[a]), h[a]));
-    sum = dd_sub(sum, dd_mul(dot, two_prod(P.beta, P.J)));
-  }
-  const dd lu = dd_log(dd_from(c.u), ln2);
-  return dd_lt(dd_add(lu, sum), dd_from(0.0));
 }
 
 // Settles the deferred sites of a colour: one warp per site, FP64 then double-double.

@@ -1,0 +1,345 @@
+// switch_dev.cuh -- per-site body of step (A) of Sec. 2.1 (potential switching), shared by
+// the single-lattice and the batched switch kernels.
+//
+// Every pair {i, i+d} survives (V -> Vbar) with probability 1 - P_ij, P_ij of Eq. (2),
+// independently.  Site i visits its half-plane list by bound thinning: element m becomes a
+// candidate with probability q_m = 1 - exp(-2 beta Vmax_m) (a Poisson process of rate
+// beta D A_m 2^-58 per element, walked over the prefix W), and a candidate survives with
+// probability (1 - P_ij) / q_m.  The draws come from Philox tag SWITCH, counter
+// (i, epoch, n/2), draw n using words 2(n%2) (exponential) and 2(n%2)+1 (survival).
+//
+// Every decision is an exact comparison of reals built from FP64 inputs.  It is taken in
+// FP64 (or FP32 in the FP32-guarded form) together with a bound on the rounding error; a
+// margin inside the bound sends the decision to double-double arithmetic.
+#pragma once
+
+#include <cstdint>
+
+#include "sco_internal.h"
+
+namespace sco {
+namespace {
+
+constexpr int kNear = 2048;  // head of the sorted list kept in shared memory (r <~ 25)
+constexpr int kStatusCapacity = 7;
+
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+struct NearTable {
+  const uint64_t* sW;
+  const uint32_t* sD;
+  const uint64_t* W;
+  const uint32_t* disp;
+  int64_t nnear, K;
+  __device__ __forceinline__ uint64_t w(int64_t k) const { return k < nnear ? sW[k] : __ldg(&W[k]); }
+  __device__ __forceinline__ uint32_t d(int64_t k) const {
+    return k < nnear ? sD[k] : __ldg(&disp[k]);
+  }
+  // first k in [lo, K) with W[k] >= target, K if none
+  __device__ __forceinline__ int64_t lower_bound(int64_t lo, uint64_t target) const {
+    if (lo < nnear) {
+      if (sW[nnear - 1] >= target) {
+        int64_t a = lo, b = nnear - 1;
+        while (a < b) {
+          const int64_t mid = (a + b) >> 1;
+          if (sW[mid] >= target) b = mid; else a = mid + 1;
+        }
+        return a;
+      }
+      lo = nnear;
+    }
+    int64_t a = lo, b = K;
+    while (a < b) {
+      const int64_t mid = (a + b) >> 1;
+      if (__ldg(&W[mid]) >= target) b = mid; else a = mid + 1;
+    }
+    return a;
+  }
+};
+
+// Exact re-evaluation of the next candidate: min { k > s : beta D 2^-58 (W_k - W_s) >= -ln u+ }.
+__device__ __noinline__ int64_t next_candidate_dd(const DevParams& P, const NearTable& T,
+                                                  int64_t s, uint64_t Ws, double up) {
+  const dd ln2 = {P.ln2_hi, P.ln2_lo};
+  const dd E = dd_neg(dd_log(dd_from(up), ln2));
+  const dd tau = dd_ldexp(dd_div(E, two_prod(P.beta, P.D)), 58);
+  int64_t a = s + 1, b = T.K;
+  while (a < b) {
+    const int64_t mid = (a + b) >> 1;
+    if (!dd_lt(dd_from_u64(T.w(mid) - Ws), tau)) b = mid; else a = mid + 1;
+  }
+  return a;
+}
+
+__device__ __forceinline__ int64_t next_candidate(const DevParams& P, const NearTable& T,
+                                                  int64_t s, uint64_t Ws, uint64_t Wtot,
+                                                  uint64_t wE, unsigned& ghits) {
+  if (s >= T.K - 1 || !(P.bD > 0.0)) return T.K;
+  const double up = u53pos(wE);
+  const double tau = -log(up) * P.inv_bD58;
+  const uint64_t rem = Wtot - Ws;
+  int64_t k = T.K;
+  if (tau <= (double)rem) k = T.lower_bound(s + 1, Ws + __double2ull_ru(tau));
+  // tau carries < 2^-49 relative error (log, fl(beta D), fl(2^58 / bD), one product): guard
+  // at 2^-46
+  const double eps = 0x1p-46;
+  bool certain = true;
+  if (k < T.K && !((double)(T.w(k) - Ws) >= tau * (1.0 + eps))) certain = false;
+  if (k - 1 > s && !((double)(T.w(k - 1) - Ws) < tau * (1.0 - eps))) certain = false;
+  if (certain) return k;
+  ++ghits;
+  return next_candidate_dd(P, T, s, Ws, up);
+}
+
+// ceil(x) as an integer for finite x >= 0 (saturating at 2^64 - 1), from the bits of x with
+// integer operations only (64-bit conversions would run on the FP64 pipe).
+__device__ __forceinline__ uint64_t ceil_u64(float x) {
+  const uint32_t b = __float_as_uint(x);
+  if (b == 0u || (b >> 31)) return 0ull;
+  const int ex = (int)((b >> 23) & 0xFFu) - 150;  // x = mant * 2^ex
+  const uint64_t mant = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
+  if (ex >= 0) return ex >= 40 ? ~0ull : mant << ex;
+  if (ex <= -25) return 1ull;  // 0 < x < 1
+  const uint64_t q = mant >> (-ex);
+  return q + ((q << (-ex)) != mant ? 1ull : 0ull);
+}
+
+// FP32 screen of the candidate search.  E = -ln u+ is taken as -log1pf(-(1 - u+)) above 1/2
+// (1 - u+ is an exact integer times 2^-53) and -logf(u+) below, so its relative error stays
+// below 2^-20.5 (one input rounding, 4 ulp of the function); tau = E fl32(2^58 / bD) adds
+// two roundings.  Margins inside 2^-18 fall through to the FP64 search.  All comparisons
+// with the uint64 prefix W are made in integers.
+__device__ __forceinline__ int64_t next_candidate_fp32(const DevParams& P, const NearTable& T,
+                                                       int64_t s, uint64_t Ws, uint64_t Wtot,
+                                                       uint64_t wE, unsigned& g32,
+                                                       unsigned& ghits) {
+  if (s >= T.K - 1 || !(P.bD > 0.0)) return T.K;
+  const uint64_t m53 = wE >> 11;  // u+ = (m53 + 1) 2^-53
+  float E;
+  if (m53 >= (1ull << 52)) {
+    const uint64_t dm = (1ull << 53) - 1ull - m53;  // < 2^52
+    const float d = __uint2float_rn((uint32_t)(dm >> 20)) * 0x1p-33f +
+                    __uint2float_rn((uint32_t)(dm & 0xFFFFFu)) * 0x1p-53f;
+    E = -log1pf(-d);
+  } else {
+    const uint64_t um = m53 + 1ull;  // <= 2^52
+    const float u = __uint2float_rn((uint32_t)(um >> 20)) * 0x1p-33f +
+                    __uint2float_rn((uint32_t)(um & 0xFFFFFu)) * 0x1p-53f;
+    E = -logf(u);
+  }
+  const float tau = E * P.inv_bD58_f;
+  const float eps = 0x1p-18f;
+  const uint64_t rem = Wtot - Ws;
+  const uint64_t thr = ceil_u64(tau);
+  int64_t k = T.K;
+  if (thr <= rem) k = T.lower_bound(s + 1, Ws + thr);
+  const uint64_t hi = ceil_u64(tau * (1.0f + eps));  // W_k - W_s >= hi: surely a candidate
+  const uint64_t lo = ceil_u64(tau * (1.0f - eps));  // W_k-1 - W_s < lo: surely not
+  bool certain = tau < 0x1p62f;
+  if (k < T.K && T.w(k) - Ws < hi) certain = false;
+  if (k - 1 > s && T.w(k - 1) - Ws >= lo) certain = false;
+  if (certain) return k;
+  ++g32;
+  return next_candidate(P, T, s, Ws, Wtot, wE, ghits);
+}
+
+// Exact survival test u q < 1 - P_ij in double-double.
+__device__ __noinline__ bool survives_dd(const DevParams& P, const double* Si, const double* Sj,
+                                         int32_t dx, int32_t dy, uint64_t A, double u1) {
+  const dd ln2 = {P.ln2_hi, P.ln2_lo};
+  const int64_t r2 = (int64_t)dx * dx + (int64_t)dy * dy;
+  const dd V = dd_pair_V(P.D, coupling_c(r2), (double)r2, Si, Sj, (double)dx, (double)dy);
+  const dd Vm = dd_vmax(P.D, A);
+  const dd b = dd_mul_d(dd_sub(V, Vm), P.beta);
+  const dd a = dd_mul_d(Vm, 2.0 * P.beta);
+  const dd pr = dd_neg(dd_expm1(b, ln2));
+  const dd q = dd_neg(dd_expm1(dd_neg(a), ln2));
+  return dd_lt(dd_mul_d(q, u1), pr);
+}
+
+// FP64 survival test with its error bound: |dV| <= 2^-47 Dc r^2, fl(Vmax) within 2^-52,
+// expm1 within 4 ulp, so 1 - P and q within the terms below (doubled for margin).
+__device__ __forceinline__ bool survives_fp64(const DevParams& P, double Dc, double Vm, double q,
+                                              double r2, const double* Si, const double* Sj,
+                                              int32_t dx, int32_t dy, uint64_t A, double u1,
+                                              unsigned& ghits) {
+  const double V = pair_V(Dc, r2, Si[0], Si[1], Si[2], Sj[0], Sj[1], Sj[2], (double)dx,
+                          (double)dy);
+  const double b = P.beta * (V - Vm);
+  const double pr = -expm1(b);  // q = -expm1(-fl(2 beta Vmax)) comes from the table
+  const double mu = pr - u1 * q;
+  const double dV = 0x1p-47 * Dc * r2;
+  const double B =
+      2.0 * (P.beta * (dV + 0x1p-52 * Vm) + 0x1p-52 * fabs(b) + 0x1p-49 * (fabs(pr) + q));
+  if (mu > B) return true;
+  if (mu < -B) return false;
+  ++ghits;
+  return survives_dd(P, Si, Sj, dx, dy, A, u1);
+}
+
+// FP32 screen of the same test (FP32-guarded form): spins from the FP32 shadow
+// (|dS| <= 2^-24 per component), table constants rounded to FP32, expm1f within 4 ulp.
+// Falls through to the FP64 test (and from there to double-double) inside the bound.
+__device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32, double Dc,
+                                              double Vm, double q64, const float* Si32,
+                                              const float* Sj32, const double* Si,
+                                              const double* Sj, int32_t dx, int32_t dy,
+                                              uint64_t A, uint64_t wU, unsigned& g32,
+                                              unsigned& ghits) {
+  const float fr2 = (float)(dx * dx + dy * dy), fx = (float)dx, fy = (float)dy;
+  // u truncated to 24 bits: 0 <= u - u24 < 2^-24, inside the 2^-19 q term of the bound
+  const float u24 = __uint2float_rn((uint32_t)(wU >> 40)) * 0x1p-24f;
+  const float ss = Si32[0] * Sj32[0] + Si32[1] * Sj32[1] + Si32[2] * Sj32[2];
+  const float pa = Si32[0] * fx + Si32[1] * fy;
+  const float pb = Sj32[0] * fx + Sj32[1] * fy;
+  const float V = t32.x * (fr2 * ss - 3.0f * (pa * pb));
+  const float beta = (float)P.beta;
+  const float b = beta * (V - t32.y);
+  const float pr = -expm1f(b);
+  const float q = t32.w;  // fl32 of the FP64 q: 2^-24 on top of its 4 ulp
+  const float mu = pr - u24 * q;
+  // |dV| <= 2^-17 Dc r^2 (shadow spins, FP32 products, constant rounding); beta and the
+  // constants carry 2^-24 each; expm1f 4 ulp; generous factor 2.
+  const float dV = 0x1p-17f * t32.x * fr2;
+  const float B = 2.0f * (beta * (dV + 0x1p-22f * t32.y) + 0x1p-21f * fabsf(b) +
+                          0x1p-19f * (fabsf(pr) + q) + 0x1p-21f * t32.z);
+  if (mu > B) return true;
+  if (mu < -B) return false;
+  ++g32;
+  return survives_fp64(P, Dc, Vm, q64, (double)dx * dx + (double)dy * dy, Si, Sj, dx, dy, A,
+                       u53(wU), ghits);
+}
+
+// Where site i writes its upper neighbours: kSlotCap slots of its own, then an overflow list
+// shared by all sites (entry: site id, j | flag).  indeg counts lower neighbours per site.
+struct SwitchOut {
+  uint32_t* slot;
+  uint32_t* indeg;
+  uint32_t* ovf;
+  uint32_t ovf_cap;
+  unsigned long long* ovf_n;
+  int* status;
+  uint32_t site_id;  // id of site i in the overflow list
+};
+
+// Switches the half-plane pairs of site i (local index) at this epoch; returns the number of
+// upper neighbours written (dipolar survivors plus exchange-only bonds).
+template <int PREC>
+__device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTable& T,
+                                                uint64_t Wtot, const double2* __restrict__ xy,
+                                                const double* __restrict__ xyq,
+                                                const float4* __restrict__ xy32,
+                                                const double* __restrict__ s,
+                                                const float* __restrict__ s32, uint32_t epoch,
+                                                int32_t mnn0, int32_t mnn1, uint32_t i,
+                                                const SwitchOut& o, unsigned long long& n_dip,
+                                                unsigned& ghits, unsigned& g32) {
+  const int32_t yi = (int32_t)site_row(i, P);
+  const int32_t xi = (int32_t)(i - (uint32_t)yi * (uint32_t)P.Lx);
+  const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
+  float Si32[3] = {0.f, 0.f, 0.f};
+  if (PREC == 1) {
+    Si32[0] = s32[i];
+    Si32[1] = s32[P.N + i];
+    Si32[2] = s32[2 * P.N + i];
+  }
+  uint32_t n_out = 0;
+  bool nn0 = false, nn1 = false;
+  auto emit = [&](uint32_t jv) {
+    if (n_out < (uint32_t)kSlotCap) {
+      o.slot[n_out] = jv;
+    } else {
+      const unsigned long long idx = atomicAdd(o.ovf_n, 1ull);
+      if (idx < o.ovf_cap) {
+        o.ovf[2 * idx] = o.site_id;
+        o.ovf[2 * idx + 1] = jv;
+      } else {
+        set_status(o.status, kStatusCapacity);
+      }
+    }
+    ++n_out;
+    atomicAdd(&o.indeg[jv & kIndexMask], 1u);
+  };
+  int64_t sidx = -1;
+  uint64_t Ws = 0;
+  W4 w;
+  for (uint64_t n = 0;; ++n) {
+    if ((n & 1) == 0) w = philox((uint64_t)i, epoch, n >> 1, kTagSwitch, P.key0, P.key1);
+    const uint64_t wE = (n & 1) ? w.w[2] : w.w[0];
+    const uint64_t wU = (n & 1) ? w.w[3] : w.w[1];
+    const int64_t k = PREC == 1 ? next_candidate_fp32(P, T, sidx, Ws, Wtot, wE, g32, ghits)
+                                : next_candidate(P, T, sidx, Ws, Wtot, wE, ghits);
+    if (k >= P.K) break;
+    const uint32_t d = T.d(k);
+    const int32_t dx = (int16_t)(d & 0xFFFFu), dy = (int32_t)(d >> 16);
+    const uint64_t Wk = T.w(k);
+    const int32_t xj = xi + dx, yj = yi + dy;
+    if (xj >= 0 && xj < P.Lx && yj < P.Ly) {
+      const int64_t j = xj + (int64_t)P.Lx * yj;
+      const uint64_t A = Wk - (k > 0 ? T.w(k - 1) : 0ull);
+      const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
+      const double2 t = __ldg(&xy[tix]);
+      const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
+      bool surv;
+      if (PREC == 1) {
+        const float Sj32[3] = {s32[j], s32[P.N + j], s32[2 * P.N + j]};
+        surv = survives_fp32(P, __ldg(&xy32[tix]), t.x, t.y, __ldg(&xyq[tix]), Si32, Sj32, Si,
+                             Sj, dx, dy, A, wU, g32, ghits);
+      } else {
+        surv = survives_fp64(P, t.x, t.y, __ldg(&xyq[tix]), (double)dx * dx + (double)dy * dy,
+                             Si, Sj, dx, dy, A, u53(wU), ghits);
+      }
+      if (surv) {
+        emit((uint32_t)j);
+        ++n_dip;
+        if (k == mnn0) nn0 = true;
+        if (k == mnn1) nn1 = true;
+      }
+    }
+    sidx = k;
+    Ws = Wk;
+  }
+  if (P.J != 0.0) {  // exchange bonds join the colouring graph
+    if (mnn0 >= 0 && !nn0 && xi + 1 < P.Lx) emit((i + 1) | kExchOnly);
+    if (mnn1 >= 0 && !nn1 && yi + 1 < P.Ly) emit((i + (uint32_t)P.Lx) | kExchOnly);
+  }
+  return n_out;
+}
+
+// Sorts one CSR row by neighbour index (insertion sort, in registers up to 64 entries);
+// returns the number of dipolar entries of the row.
+__device__ __forceinline__ unsigned sort_row(uint32_t* __restrict__ r, uint32_t n) {
+  unsigned nd = 0;
+  constexpr uint32_t kLocal = 64;
+  if (n <= kLocal) {
+    uint32_t v[kLocal];
+    for (uint32_t a = 0; a < n; ++a) {
+      const uint32_t x = r[a];
+      uint32_t c = a;
+      while (c > 0 && (v[c - 1] & kIndexMask) > (x & kIndexMask)) {
+        v[c] = v[c - 1];
+        --c;
+      }
+      v[c] = x;
+    }
+    for (uint32_t a = 0; a < n; ++a) {
+      r[a] = v[a];
+      nd += (v[a] & kExchOnly) ? 0u : 1u;
+    }
+  } else {
+    for (uint32_t a = 1; a < n; ++a) {
+      const uint32_t x = r[a];
+      uint32_t c = a;
+      while (c > 0 && (r[c - 1] & kIndexMask) > (x & kIndexMask)) {
+        r[c] = r[c - 1];
+        --c;
+      }
+      r[c] = x;
+    }
+    for (uint32_t a = 0; a < n; ++a) nd += (r[a] & kExchOnly) ? 0u : 1u;
+  }
+  return nd;
+}
+
+}  // namespace
+}  // namespace sco

@@ -97,9 +97,8 @@ __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __r
 
 }  // namespace
 
-cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches) {
+cudaError_t table_build_xy(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches) {
   cudaError_t e;
-  t.K = P.K;
   const int64_t nxy = (int64_t)P.Lx * P.Ly;
   if ((e = cudaMalloc(&t.xy, nxy * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&t.xy32, nxy * sizeof(float4))) != cudaSuccess) return e;
@@ -109,7 +108,13 @@ cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* l
   k_xy<<<(unsigned)((nxy + 255) / 256), 256, 0, s>>>(P.Lx, P.Ly, P.D, P.beta, t.xy, t.xyq,
                                                       t.xy32, t.sw64, t.sw32);
   ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t table_build_list(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches) {
+  cudaError_t e;
   const int64_t K = P.K;
+  t.K = K;
   if ((e = cudaMalloc(&t.disp, (K > 0 ? K : 1) * sizeof(uint32_t))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&t.W, (K > 0 ? K : 1) * sizeof(uint64_t))) != cudaSuccess) return e;
   if (K == 0) return cudaGetLastError();
@@ -153,14 +158,29 @@ cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* l
   return cudaGetLastError();
 }
 
-void table_free(Table& t) {
-  cudaFree(t.disp);
-  cudaFree(t.W);
+cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches) {
+  cudaError_t e = table_build_xy(P, t, s, launches);
+  if (e == cudaSuccess) e = table_build_list(P, t, s, launches);
+  return e;
+}
+
+void table_free_xy(Table& t) {
   cudaFree(t.xy);
   cudaFree(t.xy32);
   cudaFree(t.xyq);
   cudaFree(t.sw64);
   cudaFree(t.sw32);
+  t.xy = nullptr;
+  t.xy32 = nullptr;
+  t.xyq = nullptr;
+  t.sw64 = nullptr;
+  t.sw32 = nullptr;
+}
+
+void table_free(Table& t) {
+  cudaFree(t.disp);
+  cudaFree(t.W);
+  table_free_xy(t);
   t = Table();
 }
 

@@ -60,3 +60,19 @@ def test_no_device_means_error_not_fallback():
     with pytest.raises(sco.ScoError) as e:
         sco.Lattice(sco.make_params(8, T=0.5))
     assert e.value.status == sco.SCO_ECUDA
+
+
+def test_batch_arguments_rejected_before_any_device_work():
+    _build.build()
+    good = sco.make_params(8, T=0.5)
+    cases = [
+        [],                                                          # no replica
+        [good, sco.make_params(8, T=0.5, precision=sco.FP32_GUARDED)],  # mixed precision
+        [good, sco.make_params(8, T=0.5, n_sw=2)],                   # mixed n_sw
+        [good, sco.make_params(0, T=0.5)],                           # invalid replica
+        [good] * 1025,                                               # too many replicas
+    ]
+    for ps in cases:
+        with pytest.raises(sco.ScoError) as e:
+            sco.Batch(ps)
+        assert e.value.status == sco.SCO_EINVAL
