@@ -190,6 +190,10 @@ typedef struct {
   int32_t sweep_blocks_per_sm; /* resident blocks per SM of the persistent sweep, >= 1 */
   int32_t kw_blocks_per_sm;    /* resident blocks per SM of the KW level kernel, >= 1 */
   int32_t use_graph;           /* 1: capture and replay graphs; 0: launch directly */
+  int32_t kw_schedule;         /* 0: all KW levels in one kernel, vertices bucketed by colour
+                                  and reduced largest colour first (order of Sec. 2.3.2 (2));
+                                  1: one kernel per level, each vertex recolours as soon as
+                                  its larger neighbours are done (2)'.  Same colours. */
 } sco_batch_tuning;
 
 /* Creates a batch of n_replicas lattices from p[0 .. n_replicas-1] (1 <= n_replicas <= 1024,

@@ -239,7 +239,8 @@ sco_status do_colour(sco_ctx* c) {
     cudaFree(c->cb.scan_tmp);
     cudaFree(c->cb.tile_cnt);
     cudaFree(c->cb.dcnt);
-    c->cb.hist = c->cb.off = c->cb.cursor = c->cb.tile_cnt = c->cb.dcnt = nullptr;
+    cudaFree(c->cb.bcnt);
+    c->cb.hist = c->cb.off = c->cb.cursor = c->cb.tile_cnt = c->cb.dcnt = c->cb.bcnt = nullptr;
     c->cb.scan_tmp = nullptr;
     const uint32_t cap = c->g + 64;
     const int64_t ntiles = (c->P.N + kClassTileSites - 1) / kClassTileSites;
@@ -248,6 +249,7 @@ sco_status do_colour(sco_ctx* c) {
     SCO_TRY(cudaMalloc(&c->cb.off, (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.cursor, (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.dcnt, (cap + 1) * sizeof(uint32_t)));
+    SCO_TRY(cudaMalloc(&c->cb.bcnt, (size_t)32 * (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.tile_cnt, tc * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.scan_tmp, scan_tmp_bytes(tc > cap + 1 ? tc : cap + 1)));
     c->cls_cap = cap;
@@ -293,6 +295,8 @@ void free_all(sco_ctx* c) {
   cudaFree(c->cb.perm);
   cudaFree(c->cb.tile_cnt);
   cudaFree(c->cb.scan_tmp);
+  cudaFree(c->cb.bcnt);
+  cudaFree(c->cb.meta);
   cudaFree(c->acc);
   cudaFree(c->defer);
   cudaFree(c->cnt);
@@ -359,6 +363,7 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.blk, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.colour, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.perm, N * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cb.meta, 8 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->acc, N);
   if (e == cudaSuccess) e = cudaMalloc(&c->defer, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cnt, sizeof(DevCounters));

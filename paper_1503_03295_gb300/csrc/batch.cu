@@ -17,6 +17,8 @@
 #include <cstdint>
 
 #include "batch.h"
+#include "grid_dev.cuh"
+#include "kw_bcr.cuh"
 #include "kw_dev.cuh"
 #include "sweep_dev.cuh"
 #include "switch_dev.cuh"
@@ -37,105 +39,9 @@ __device__ __forceinline__ bool block_halted(const BatchDev& B) {
   return h != 0;
 }
 
-// Largest r in [0, n) with a[r] <= x (a[0] <= x, a non-decreasing).
-__device__ __forceinline__ int find_le(const uint32_t* a, int n, uint32_t x) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int m = (lo + hi + 1) >> 1;
-    if (a[m] <= x) lo = m;
-    else hi = m - 1;
-  }
-  return lo;
-}
-
 // Replica of this block in the per-site launches (kBatchBlock sites per block).
 __device__ __forceinline__ int block_replica(const BatchDev& B) {
   return find_le(B.blk_start, B.R, blockIdx.x);
-}
-
-__device__ __forceinline__ uint32_t ld_u32_gpu(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid-wide barrier of a cooperative launch (all blocks resident).  The wait is bounded:
-// after ns_limit, or once another block reported an error, the block gives up, sets
-// SCO_ETIMEOUT and returns false.
-__device__ bool grid_sync(BatchCtl* ctl, unsigned long long ns_limit) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned gen = ld_acquire_u32(&ctl->bar_gen);
-    __threadfence();
-    if (atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1) {
-      ctl->bar_count = 0;
-      __threadfence();
-      st_release_u32(&ctl->bar_gen, gen + 1);
-    } else {
-      const unsigned long long t0 = global_ns();
-      unsigned spins = 0, nap = 32;
-      while (ld_acquire_u32(&ctl->bar_gen) == gen) {
-        __nanosleep(nap);
-        nap = nap < 256 ? 2 * nap : 256;
-        if ((++spins & 63) == 0 &&
-            (global_ns() - t0 > ns_limit || ld_status(&ctl->status) != 0)) {
-          atomicCAS(&ctl->status, 0, kStatusTimeout);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-__device__ __forceinline__ void smem_copy(void* dst, const void* src, int bytes) {
-  for (int k = threadIdx.x; k < bytes / 4; k += blockDim.x)
-    static_cast<uint32_t*>(dst)[k] = static_cast<const uint32_t*>(src)[k];
-}
-
-// Exclusive scan of a[0..n) in place, a[n] = total; blockDim.x == 256, n <= 1024.
-__device__ void block_scan_excl(uint32_t* a, int n) {
-  __shared__ uint32_t wsum[8];
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  uint32_t v[4], s = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int q = 4 * t + k;
-    v[k] = q < n ? a[q] : 0u;
-    s += v[k];
-  }
-  uint32_t x = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  uint32_t run = x - s;
-  for (int k = 0; k < w; ++k) run += wsum[k];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int q = 4 * t + k;
-    if (q < n) a[q] = run;
-    run += v[k];
-  }
-  if (t == 255) a[n] = run;
-  __syncthreads();
 }
 
 // ---- step (A): switch + CSR -------------------------------------------------------------
@@ -380,26 +286,42 @@ __global__ void __launch_bounds__(256, 4) kb_kw_level(const BatchDev B, unsigned
   };
   unsigned nap = 64;
   if (m <= 32) {
-    uint32_t vtx[32];
+    // global vertex, colour before the level, and the global index of the neighbour it waits
+    // for (kNone: none recorded), per owned slot
+    uint32_t vtx[32], cv[32], wt[32];
     unsigned pend = 0;
 #pragma unroll
     for (int a = 0; a < 32; ++a) {
       vtx[a] = kNone;
+      wt[a] = kNone;
+      cv[a] = 0;
       if ((uint32_t)a < m) {
         vtx[a] = vertex_of(tid + a * nth);
-        if (vtx[a] != kNone) pend |= 1u << a;
+        if (vtx[a] != kNone) {
+          cv[a] = (uint32_t)(B.word[vtx[a]] & kColMask);
+          pend |= 1u << a;
+        }
       }
     }
     for (unsigned long long pass = 0; pend; ++pass) {
       bool progress = false;
-      unsigned todo = pend;
-      while (todo) {
-        const int a = __ffs(todo) - 1;
-        todo &= todo - 1;
-        bool done;
-        if (attempt(vtx[a], done) && done) {
+      unsigned ready = kw_ready(pend, wt, B.word, p);
+      while (ready) {
+        const int a = __ffs(ready) - 1;
+        ready &= ready - 1;
+        const uint32_t gv = vtx[a];
+        const int r = find_le(sbase, R, gv);
+        const uint32_t base = sbase[r];
+        unsigned rm = 0;
+        const uint32_t w = kw_attempt(gv - base, cv[a], p, B.plan[r].magic, B.row_ptr + base,
+                                      B.col, B.word + base, rm);
+        if (w == kNone) {
+          atomicMax(&smax[r], rm);
           pend &= ~(1u << a);
           progress = true;
+          wt[a] = kNone;
+        } else {
+          wt[a] = base + w;
         }
       }
       if (!pend) break;
@@ -586,7 +508,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) kb_sweep(const BatchDe
       }
       write_site(P, x, dec == 1, s, PREC == 1 ? s32 : nullptr, B.acc + base);
     }
-    if (!grid_sync(B.ctl, B.ns_limit)) break;
+    if (!grid_sync(B.ctl->bar, &B.ctl->status, B.ns_limit)) break;
     const uint32_t nd = ld_u32_gpu(&B.dcnt[c]);
     if (nd == 0) continue;
     for (uint32_t q = gwarp; q < nd; q += nwarps) {
@@ -609,7 +531,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) kb_sweep(const BatchDe
       if (lane == 0) write_site(P, x, dec == 1, s, PREC == 1 ? s32 : nullptr, B.acc + base);
       __syncwarp();
     }
-    if (!grid_sync(B.ctl, B.ns_limit)) break;
+    if (!grid_sync(B.ctl->bar, &B.ctl->status, B.ns_limit)) break;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
@@ -649,12 +571,13 @@ size_t kw_smem(int R) { return (size_t)(3 * R + 2) * sizeof(uint32_t); }
 
 size_t batch_sweep_smem(int R) { return (size_t)(3 * R + 1) * sizeof(uint32_t); }
 
-int batch_kw_occupancy() {
+int batch_kw_occupancy(int schedule, int R, unsigned pal) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_kw_level, 256, kw_smem(kMaxReplicas)) !=
-          cudaSuccess ||
-      n < 1)
-    n = 1;
+  const cudaError_t e =
+      schedule == 0 && pal <= kBcrMaxPalette
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_kw_bcr, 256, kw_bcr_smem(R, pal))
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_kw_level, 256, kw_smem(R));
+  if (e != cudaSuccess || n < 1) n = 1;
   return n;
 }
 
@@ -700,11 +623,37 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
     return e;
   kb_kw_init<<<B.nblocks, kBatchBlock, 0, st>>>(B);
   ++*L.launches;
-  for (unsigned p = 1; p <= L.levels; ++p) {
-    if ((e = launch_coop(kb_kw_level, (unsigned)L.kw_grid, 256, kw_smem(B.R), st, B, p)) !=
-        cudaSuccess)
+  if (L.kw_schedule == 0 && B.pal_cap <= kBcrMaxPalette && L.levels < kBcrMaxLevels) {
+    if ((e = cudaMemsetAsync(B.bcnt, 0, (size_t)kBcrMaxLevels * B.pal_cap * sizeof(uint32_t),
+                             st)) != cudaSuccess)
+      return e;
+    KwView V{};
+    V.R = B.R;
+    V.site_start = B.site_start;
+    V.plan = B.plan;
+    V.row_ptr = B.row_ptr;
+    V.col = B.col;
+    V.word = B.word;
+    V.list = B.blk;
+    V.bcnt = B.bcnt;
+    V.cnt = B.cnt;
+    V.bar = B.ctl->bar;
+    V.status = &B.ctl->status;
+    V.halt = &B.ctl->flag;
+    V.pal = B.pal_cap;
+    V.levels = L.levels;
+    V.ns_limit = B.ns_limit;
+    if ((e = launch_coop(k_kw_bcr, (unsigned)L.kw_grid, 256, kw_bcr_smem(B.R, B.pal_cap), st,
+                         V)) != cudaSuccess)
       return e;
     ++*L.launches;
+  } else {
+    for (unsigned p = 1; p <= L.levels; ++p) {
+      if ((e = launch_coop(kb_kw_level, (unsigned)L.kw_grid, 256, kw_smem(B.R), st, B, p)) !=
+          cudaSuccess)
+        return e;
+      ++*L.launches;
+    }
   }
   kb_kw_final<<<B.nblocks, kBatchBlock, nw * sizeof(uint32_t), st>>>(B);
   kb_colour_stats<<<1, 1024, 0, st>>>(B);

@@ -52,7 +52,7 @@ struct BatchCtl {
   int status;                   // sticky device error (sco_status), e.g. a wait gave up
   unsigned gmax;                // max palette over replicas this epoch
   unsigned lmax;                // max KW levels over replicas this epoch
-  unsigned bar_count, bar_gen;  // grid barrier of the persistent sweep
+  unsigned bar[2];              // grid barrier of the persistent kernels (count, generation)
   unsigned pad;
 };
 constexpr int kReplanCol = 1, kReplanOvf = 2, kReplanPal = 4;
@@ -95,6 +95,7 @@ struct BatchDev {
   uint32_t* off;       // pal_cap + 1 class offsets
   uint32_t* defer;     // Ntot
   uint32_t* dcnt;      // pal_cap
+  uint32_t* bcnt;      // 32 x pal_cap KW bucket sizes per level
   unsigned long long ns_limit;  // bound of every device-side wait
 };
 
@@ -104,7 +105,8 @@ DevParams make_dev_params(const sco_params& p);
 
 // Launchers (batch.cu).  Each enqueues one phase for every replica on `st`.
 struct BatchLaunch {
-  int kw_grid;     // blocks of the persistent KW level kernel
+  int kw_schedule;  // 0: all levels in one kernel, buckets by colour; 1: one async kernel per level
+  int kw_grid;     // blocks of the persistent KW kernel(s)
   int sweep_grid;  // blocks of the persistent sweep kernel
   unsigned levels;  // KW level launches per colouring (>= every replica's M)
   uint64_t* scan_tmp;
@@ -115,7 +117,7 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
 cudaError_t batch_sweep(const BatchDev& B, const BatchLaunch& L, cudaStream_t st);
 cudaError_t batch_step_end(const BatchDev& B, const BatchLaunch& L, cudaStream_t st);
 // co-resident blocks per SM of the two persistent kernels (for the grid sizes)
-int batch_kw_occupancy();
+int batch_kw_occupancy(int schedule, int R, unsigned pal);
 int batch_sweep_occupancy(int precision, int R);
 size_t batch_sweep_smem(int R);
 

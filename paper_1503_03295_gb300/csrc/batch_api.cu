@@ -97,6 +97,7 @@ void free_all(sco_batch* b) {
   cudaFree(B.off);
   cudaFree(B.defer);
   cudaFree(B.dcnt);
+  cudaFree(B.bcnt);
   cudaFree(b->L.scan_tmp);
   for (auto& t : b->xy) table_free_xy(t);
   for (auto& t : b->lists) table_free(t);
@@ -112,12 +113,14 @@ cudaError_t alloc_palette(sco_batch* b, uint32_t pal) {
   cudaFree(B.tile_cnt);
   cudaFree(B.off);
   cudaFree(B.dcnt);
-  B.used = B.tile_cnt = B.off = B.dcnt = nullptr;
+  cudaFree(B.bcnt);
+  B.used = B.tile_cnt = B.off = B.dcnt = B.bcnt = nullptr;
   B.pal_cap = pal;
   cudaError_t e = cudaMalloc(&B.used, (size_t)b->R * (pal / 32) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&B.tile_cnt, ((size_t)pal * B.ntiles + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&B.off, (pal + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&B.dcnt, pal * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&B.bcnt, (size_t)32 * pal * sizeof(uint32_t));
   const size_t need = std::max((size_t)B.Ntot + 1, (size_t)pal * B.ntiles + 1);
   if (e == cudaSuccess && need > b->scan_tmp_n) {
     cudaFree(b->L.scan_tmp);
@@ -130,6 +133,8 @@ cudaError_t alloc_palette(sco_batch* b, uint32_t pal) {
 
 void set_grids(sco_batch* b) {
   const int sms = num_sms();
+  b->L.kw_schedule = b->tune.kw_schedule;
+  b->kw_occ = batch_kw_occupancy(b->tune.kw_schedule, b->R, b->B.pal_cap);
   b->L.kw_grid = std::min(b->tune.kw_blocks_per_sm, b->kw_occ) * sms;
   b->L.sweep_grid = std::min(b->tune.sweep_blocks_per_sm, b->sweep_occ) * sms;
 }
@@ -215,6 +220,7 @@ sco_status replan(sco_batch* b) {
     if (pal > kPalMax) pal = kPalMax;
     if (h.gmax > pal) return SCO_ECAPACITY;
     SCO_TRY(alloc_palette(b, pal));
+    set_grids(b);
   }
   SCO_TRY(cudaMemsetAsync(&B.ctl->flag, 0, sizeof(int), b->st));
   SCO_TRY(cudaStreamSynchronize(b->st));
@@ -261,7 +267,7 @@ sco_status run_steps(sco_batch* b, int64_t n) {
 bool valid_tuning(const sco_batch_tuning* t) {
   return t && t->steps_per_graph >= 1 && t->steps_per_graph <= 1024 &&
          t->sweep_blocks_per_sm >= 1 && t->kw_blocks_per_sm >= 1 &&
-         (t->use_graph == 0 || t->use_graph == 1);
+         (t->use_graph == 0 || t->use_graph == 1) && (t->kw_schedule == 0 || t->kw_schedule == 1);
 }
 
 bool same_model(const sco_params& a, const sco_params& b) {
@@ -416,7 +422,8 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return fail(from_cuda(e));
-  b->kw_occ = batch_kw_occupancy();
+  b->tune.kw_schedule = 0;
+  b->kw_occ = batch_kw_occupancy(0, n, B.pal_cap);
   b->sweep_occ = batch_sweep_occupancy(B.precision, n);
   b->tune.steps_per_graph = 4;
   b->tune.sweep_blocks_per_sm = b->sweep_occ;
@@ -443,12 +450,13 @@ sco_status sco_batch_set_tuning(sco_batch* b, const sco_batch_tuning* t) {
   if (!b || !valid_tuning(t)) return SCO_EINVAL;
   SCO_TRY(cudaStreamSynchronize(b->st));
   const bool grids = t->sweep_blocks_per_sm != b->tune.sweep_blocks_per_sm ||
-                     t->kw_blocks_per_sm != b->tune.kw_blocks_per_sm;
+                     t->kw_blocks_per_sm != b->tune.kw_blocks_per_sm ||
+                     t->kw_schedule != b->tune.kw_schedule;
   b->tune = *t;
   b->tune.sweep_blocks_per_sm = std::min(t->sweep_blocks_per_sm, b->sweep_occ);
-  b->tune.kw_blocks_per_sm = std::min(t->kw_blocks_per_sm, b->kw_occ);
   if (grids) drop_graphs(b);
   set_grids(b);
+  b->tune.kw_blocks_per_sm = std::min(t->kw_blocks_per_sm, b->kw_occ);
   return SCO_OK;
 }
 
@@ -507,9 +515,14 @@ sco_status sco_batch_autotune(sco_batch* b, int32_t trial, sco_batch_tuning* cho
     try_dim(c);
   }
   {
+    sco_batch_tuning t = best;
+    t.kw_schedule = 1 - best.kw_schedule;
+    try_dim({t});
+  }
+  {
     std::vector<sco_batch_tuning> c;
     for (int v : {1, 2, 4})
-      if (v <= b->kw_occ && v != best.kw_blocks_per_sm) {
+      if (v != best.kw_blocks_per_sm) {
         sco_batch_tuning t = best;
         t.kw_blocks_per_sm = v;
         c.push_back(t);

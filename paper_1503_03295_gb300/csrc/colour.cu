@@ -18,6 +18,7 @@
 // same colours as the synchronous rounds, and t_R recovered from the per-vertex rounds.
 #include <cstdint>
 
+#include "kw_bcr.cuh"
 #include "kw_dev.cuh"
 
 namespace sco {
@@ -51,32 +52,32 @@ __global__ void __launch_bounds__(256, 4) k_kw_level(uint32_t N, uint32_t g, uns
   unsigned rmax = 0;
   unsigned nap = 64;  // back-off (ns) while nothing of this thread can progress
   if (m <= 32) {
-    // one bit per unfinished owned vertex: waiting passes touch only pending vertices
-    uint32_t vtx[32];
+    // one bit per unfinished owned vertex; the vertex, its colour before the level and the
+    // neighbour it waits for (kNone: none recorded) stay with the thread
+    uint32_t vtx[32], cv[32], wt[32];
     unsigned pend = 0;
 #pragma unroll
     for (int a = 0; a < 32; ++a) {
       vtx[a] = kNone;
+      wt[a] = kNone;
+      cv[a] = 0;
       if ((uint32_t)a < m) {
         const uint32_t v = kw_vertex(tid + a * nth, half, p, M);
         if (v < N) {
           vtx[a] = v;
+          cv[a] = (uint32_t)(word[v] & kColMask);
           pend |= 1u << a;
         }
       }
     }
     for (unsigned long long pass = 0; pend; ++pass) {
       bool progress = false;
-      unsigned todo = pend;
-      while (todo) {
-        const int a = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint32_t v = vtx[a];
-        const uint32_t b = blk[v];
-        if (b != kNone && tag_of(ld_relaxed(&word[b])) != p) continue;  // blocker unfinished
-        const uint32_t w = kw_attempt(v, (uint32_t)(word[v] & kColMask), p, M, row_ptr, col,
-                                      word, rmax);
-        blk[v] = w;
+      unsigned ready = kw_ready(pend, wt, word, p);
+      while (ready) {
+        const int a = __ffs(ready) - 1;
+        ready &= ready - 1;
+        const uint32_t w = kw_attempt(vtx[a], cv[a], p, M, row_ptr, col, word, rmax);
+        wt[a] = w;
         if (w == kNone) {
           pend &= ~(1u << a);
           progress = true;
@@ -131,141 +132,6 @@ __global__ void __launch_bounds__(256, 4) k_kw_level(uint32_t N, uint32_t g, uns
         break;
       }
     }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) rmax = max(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
-  if ((threadIdx.x & 31) == 0 && rmax) atomicMax(&cnt->lev_rounds[p & 31], rmax);
-}
-
-// Block-phased KW level (the default).  Block b owns a contiguous range of right-half
-// slots, buckets its vertices by previous colour in shared memory, and processes the buckets
-// from the largest colour down with a block barrier between colours -- the order of plain
-// BCR, which gives the same colouring.  A larger same-group neighbour owned by another block
-// may still be unfinished: the thread waits for that one word (bounded).  No deadlock: a
-// thread of a block at colour c only waits for a block still at a larger colour, and with
-// every block resident the block at the largest colour never waits.
-__device__ __forceinline__ bool kw_wait(const unsigned long long* word, uint32_t u, unsigned p,
-                                        unsigned long long& wu, unsigned long long t_start,
-                                        unsigned long long ns_limit, DevCounters* cnt) {
-  unsigned spins = 0;
-  unsigned nap = 32;
-  while (tag_of(wu) != p) {
-    __nanosleep(nap);
-    nap = nap < 1024 ? 2 * nap : 1024;
-    wu = ld_relaxed(&word[u]);
-    if ((++spins & 31) == 0 &&
-        (global_ns() - t_start > ns_limit || ld_status(&cnt->status) != 0)) {
-      atomicCAS(&cnt->status, 0, kStatusTimeout);
-      return false;
-    }
-  }
-  return true;
-}
-
-__global__ void __launch_bounds__(256) k_kw_level_phased(uint32_t N, uint32_t g,
-                                                          unsigned long long M, unsigned p,
-                                                          uint32_t chunk,
-                                                          const uint32_t* __restrict__ row_ptr,
-                                                          const uint32_t* __restrict__ col,
-                                                          unsigned long long* word,
-                                                          DevCounters* __restrict__ cnt,
-                                                          unsigned long long ns_limit) {
-  extern __shared__ uint32_t sm[];
-  uint32_t* ids = sm;              // chunk vertex ids, bucketed by previous colour
-  uint32_t* start = sm + chunk;    // g + 1 bucket starts
-  uint32_t* fill = start + g + 1;  // g bucket cursors
-  __shared__ int abort_flag;
-  const unsigned long long t_start = global_ns();
-  const uint32_t half = g << (p - 1);
-  const uint32_t ngroups = (uint32_t)(((unsigned long long)N + ((unsigned long long)g << p) - 1) /
-                                      ((unsigned long long)g << p));
-  const uint32_t R = ngroups * half;
-  const uint32_t r0 = blockIdx.x * chunk;
-  const uint32_t r1 = min(R, r0 + chunk);
-  if (threadIdx.x == 0) abort_flag = 0;
-  for (uint32_t c = threadIdx.x; c <= g; c += blockDim.x) start[c] = 0;
-  __syncthreads();
-  for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    const uint32_t v = kw_vertex(r, half, p, M);
-    if (v < N) atomicAdd(&start[(uint32_t)(word[v] & kColMask) + 1], 1u);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {  // exclusive scan of g small counts
-    uint32_t acc = 0;
-    for (uint32_t c = 0; c <= g; ++c) {
-      acc += start[c];
-      start[c] = acc;
-    }
-  }
-  __syncthreads();
-  for (uint32_t c = threadIdx.x; c < g; c += blockDim.x) fill[c] = start[c];
-  __syncthreads();
-  for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    const uint32_t v = kw_vertex(r, half, p, M);
-    if (v < N) ids[atomicAdd(&fill[(uint32_t)(word[v] & kColMask)], 1u)] = v;
-  }
-  __syncthreads();
-  unsigned rmax = 0;
-  for (int c = (int)g - 1; c >= 0; --c) {
-    const uint32_t b0 = start[c], b1 = start[c + 1];
-    for (uint32_t q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
-      const uint32_t v = ids[q];
-      const uint32_t cv = (uint32_t)c;
-      const uint32_t grp = fdiv(v, M) >> p;
-      const uint32_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
-      unsigned long long used[4] = {0, 0, 0, 0};  // colours < 256 (mex <= degree)
-      unsigned rv = 0;
-      bool ok = true;
-      for (uint32_t q0 = e0; q0 < e1 && ok; q0 += 8) {
-        uint32_t uu[8];
-        unsigned long long ww[8];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) uu[a] = q0 + a < e1 ? (col[q0 + a] & kIndexMask) : kNone;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          ww[a] = 0;
-          if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) ww[a] = ld_relaxed(&word[uu[a]]);
-          else uu[a] = kNone;
-        }
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          if (uu[a] == kNone) continue;
-          unsigned long long wu = ww[a];
-          const bool right = (fdiv(uu[a], M) >> (p - 1)) & 1u;
-          if (right && tag_of(wu) != p) {
-            if ((uint32_t)(wu & kColMask) < cv) continue;  // smaller: colour >= g for now
-            // larger and owned by another block that has not reached it yet
-            if (!kw_wait(word, uu[a], p, wu, t_start, ns_limit, cnt)) {
-              ok = false;
-              break;
-            }
-          }
-          const uint32_t cu = (uint32_t)(wu & kColMask);
-          if (right) rv = max(rv, rnd_of(wu));
-          if (cu < 256) used[cu >> 6] |= 1ull << (cu & 63);
-        }
-      }
-      if (!ok) {
-        abort_flag = 1;
-        break;
-      }
-      unsigned cn = 0;
-      if (e1 - e0 < 256) {
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          if (~used[w]) {
-            cn = 64 * w + __ffsll((long long)~used[w]) - 1;
-            break;
-          }
-        }
-      } else {
-        cn = mex_slow(v, p, M, row_ptr, col, word);
-      }
-      rmax = max(rmax, rv + 1);
-      st_relaxed(&word[v], pack(p, rv + 1, cn));
-    }
-    __syncthreads();
-    if (abort_flag) break;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) rmax = max(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
@@ -378,6 +244,14 @@ __global__ void k_scatter(int64_t N, const uint32_t* __restrict__ colour,
   if (ok) perm[off[c] + base + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)v;
 }
 
+// Parameters of the one-lattice view of the persistent colouring kernel.
+__global__ void k_kw_meta(uint32_t N, uint32_t g, unsigned levels, unsigned long long magic,
+                          uint32_t* site_start, RepPlan* plan) {
+  site_start[0] = 0;
+  site_start[1] = N;
+  plan[0] = RepPlan{g, levels, magic};
+}
+
 }  // namespace
 
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
@@ -392,44 +266,48 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   const unsigned nb = (unsigned)((N + 255) / 256);
   k_kw_init<<<nb, 256, 0, st>>>(N, g, b.word, b.blk);
   ++*launches;
-  const unsigned long long ns_limit = 2000000000ull;  // 2 s per level
+  const unsigned long long ns_limit = 2000000000ull;  // 2 s per wait
   unsigned long long magic = div_magic(g);
-  // block-phased levels when every block's bucket of vertices fits in its shared memory
-  constexpr size_t kPhasedSmem = 24 * 1024;  // bytes of dynamic shared memory per block
-  static int phased_bps = 0;
-  if (phased_bps == 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&phased_bps, k_kw_level_phased, 256,
-                                                      kPhasedSmem);
+  // Large lattices: all levels in one persistent kernel, buckets of equal previous colour in
+  // turn (each thread would otherwise own many vertices per level).  Small ones: one kernel
+  // per level in which a vertex recolours as soon as its larger neighbours are done (about g
+  // grid barriers per level would dominate there).
+  if (N >= (1 << 20) && M > 0 && g <= kBcrMaxPalette && M < kBcrMaxLevels) {
+    const size_t sh = kw_bcr_smem(1, g);
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_kw_bcr, 256, sh);
     if (e != cudaSuccess) return e;
-    if (phased_bps < 1) phased_bps = 1;
-  }
-  const int64_t pgrid = (int64_t)phased_bps * num_sms();
-  bool phased = true;
-  int64_t max_chunk = 0;
-  for (unsigned p = 1; p <= M; ++p) {
-    const int64_t gsz = (int64_t)g << p, hf = (int64_t)g << (p - 1);
-    const int64_t R = (N + gsz - 1) / gsz * hf;
-    const int64_t ch = (R + pgrid - 1) / pgrid;
-    if (ch > max_chunk) max_chunk = ch;
-  }
-  const size_t need = (size_t)(max_chunk + 2 * (int64_t)g + 2) * sizeof(uint32_t);
-  if (need > kPhasedSmem) phased = false;
-  if (phased) {
-    for (unsigned p = 1; p <= M; ++p) {
-      const int64_t gsz = (int64_t)g << p, hf = (int64_t)g << (p - 1);
-      const int64_t R = (N + gsz - 1) / gsz * hf;
-      uint32_t chunk = (uint32_t)((R + pgrid - 1) / pgrid);
-      const size_t sh = (size_t)(chunk + 2 * (size_t)g + 2) * sizeof(uint32_t);
-      uint32_t Nn = (uint32_t)N, gg = g;
-      unsigned pp = p;
-      unsigned long long lim = ns_limit;
-      void* args[] = {(void*)&Nn, (void*)&gg, (void*)&magic, (void*)&pp, (void*)&chunk,
-                      (void*)&row_ptr, (void*)&col, (void*)&b.word, (void*)&cnt, (void*)&lim};
-      e = cudaLaunchCooperativeKernel((const void*)k_kw_level_phased, dim3((unsigned)pgrid),
-                                      dim3(256), args, sh, st);
-      if (e != cudaSuccess) return e;
-      ++*launches;
-    }
+    if (bps > 4) bps = 4;
+    if (bps < 1) bps = 1;
+    if ((e = cudaMemsetAsync(b.bcnt, 0, (size_t)kBcrMaxLevels * g * sizeof(uint32_t), st)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaMemsetAsync(cnt->bar, 0, sizeof(cnt->bar), st)) != cudaSuccess) return e;
+    uint32_t* site_start = reinterpret_cast<uint32_t*>(b.meta);
+    RepPlan* plan = reinterpret_cast<RepPlan*>(b.meta + 2);
+    k_kw_meta<<<1, 1, 0, st>>>((uint32_t)N, g, M, magic, site_start, plan);
+    ++*launches;
+    KwView V{};
+    V.R = 1;
+    V.site_start = site_start;
+    V.plan = plan;
+    V.row_ptr = row_ptr;
+    V.col = col;
+    V.word = b.word;
+    V.list = b.blk;
+    V.bcnt = b.bcnt;
+    V.cnt = cnt;
+    V.bar = cnt->bar;
+    V.status = &cnt->status;
+    V.halt = nullptr;
+    V.pal = g;
+    V.levels = M;
+    V.ns_limit = ns_limit;
+    void* args[] = {(void*)&V};
+    e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr, dim3((unsigned)(bps * num_sms())),
+                                    dim3(256), args, sh, st);
+    if (e != cudaSuccess) return e;
+    ++*launches;
     k_kw_final<<<nb, 256, 0, st>>>(N, M, g, variant, b.word, b.colour, cnt);
     ++*launches;
     return cudaGetLastError();

@@ -1,0 +1,253 @@
+// kw_bcr.cuh -- all levels of the Kuhn-Wattenhofer colouring (Sec. 2.3.3) in one persistent
+// cooperative kernel.  At each level the right-half vertices are bucketed by their colour
+// from the previous level, and the buckets are processed from the largest colour down, one
+// grid barrier apart: the order of plain colour reduction (2) of Sec. 2.3.2.
+//
+// When bucket c runs, every same-group right-half neighbour of larger previous colour has
+// taken its new colour and the smaller ones still hold colours >= g (ignored), so each vertex
+// of the bucket recolours at once to the smallest colour not held by a final same-group
+// neighbour, with round 1 + the largest round among the larger ones.  That is the
+// order-independent result of the modified reduction (2)': the same colouring and the same
+// t_R as the synchronous rounds, for one lattice or a batch of them.
+#pragma once
+
+#include <cstdint>
+
+#include "batch.h"
+#include "grid_dev.cuh"
+#include "kw_dev.cuh"
+
+namespace sco {
+namespace {
+
+constexpr unsigned kBcrMaxPalette = 2048;  // bucket counters kept in shared memory
+constexpr unsigned kBcrMaxLevels = 32;
+
+struct KwView {
+  int R;                        // lattices (1 for a single lattice)
+  const uint32_t* site_start;   // R + 1 first vertex of each lattice
+  const RepPlan* plan;          // R: g, levels, magic
+  const uint32_t* row_ptr;      // global entry offsets; col entries lattice-local
+  const uint32_t* col;
+  unsigned long long* word;     // packed (level, round, colour), global vertex index
+  uint32_t* list;               // bucketed right-half vertices of the current level
+  uint32_t* bcnt;               // kBcrMaxLevels x pal bucket sizes, zero on entry
+  DevCounters* cnt;             // R: lev_rounds
+  unsigned* bar;                // grid barrier words
+  int* status;                  // sticky error word
+  const int* halt;              // optional: nonzero on entry -> return at once
+  unsigned pal;                 // >= every g, <= kBcrMaxPalette
+  unsigned levels;              // >= every M, <= kBcrMaxLevels - 1
+  unsigned long long ns_limit;  // bound of every barrier wait
+};
+
+// The row of a vertex with its first sixteen neighbour entries, loaded ahead of its turn.
+struct KwRow {
+  uint32_t gv;  // global vertex (kNone: no item)
+  uint32_t b, e;
+  uint32_t uu[16];
+};
+
+__device__ __forceinline__ void kw_fetch(KwRow& w, uint32_t gv, const uint32_t* __restrict__ row_ptr,
+                                         const uint32_t* __restrict__ col) {
+  w.gv = gv;
+  if (gv == kNone) return;
+  w.b = row_ptr[gv];
+  w.e = row_ptr[gv + 1];
+#pragma unroll
+  for (int a = 0; a < 16; ++a) w.uu[a] = w.b + a < w.e ? (col[w.b + a] & kIndexMask) : kNone;
+}
+
+// Recolours v (lattice-local; its row fetched in w) of previous colour c: the smallest colour
+// not held by a final same-group neighbour, round 1 + the largest round among the right-half
+// ones.  A same-group right-half neighbour of larger previous colour that is not done yet
+// (which the bucket order rules out) would be waited for, bounded (false on timeout or
+// error).  Neighbour words are loaded sixteen at a time, back to back.
+__device__ __forceinline__ bool kw_recolour(uint32_t v, uint32_t c, const KwRow& w, unsigned p,
+                                            unsigned long long M,
+                                            const uint32_t* __restrict__ col,
+                                            unsigned long long* word, unsigned& rmax,
+                                            int* status, unsigned long long t_start,
+                                            unsigned long long ns_limit) {
+  const uint32_t grp = fdiv(v, M) >> p;
+  const uint32_t b = w.b, e = w.e;
+  unsigned long long used[4] = {0, 0, 0, 0};  // colours < 256 (mex <= degree)
+  unsigned rv = 0;
+  for (uint32_t q0 = b; q0 < e; q0 += 16) {
+    uint32_t uu[16];
+    unsigned long long ww[16];
+    if (q0 == b) {
+#pragma unroll
+      for (int a = 0; a < 16; ++a) uu[a] = w.uu[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 16; ++a) uu[a] = q0 + a < e ? (col[q0 + a] & kIndexMask) : kNone;
+    }
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+      ww[a] = 0;
+      if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) ww[a] = ld_relaxed(&word[uu[a]]);
+      else uu[a] = kNone;
+    }
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+      if (uu[a] == kNone) continue;
+      unsigned long long wu = ww[a];
+      const bool right = (fdiv(uu[a], M) >> (p - 1)) & 1u;
+      if (right && tag_of(wu) != p) {
+        if ((uint32_t)(wu & kColMask) < c) continue;  // smaller: still >= g
+        unsigned spins = 0;
+        while (tag_of(wu) != p) {
+          __nanosleep(64);
+          wu = ld_relaxed(&word[uu[a]]);
+          if ((++spins & 255) == 0 &&
+              (global_ns() - t_start > ns_limit || ld_status(status) != 0)) {
+            atomicCAS(status, 0, kStatusTimeout);
+            return false;
+          }
+        }
+      }
+      const uint32_t cu = (uint32_t)(wu & kColMask);
+      if (right) rv = max(rv, rnd_of(wu));
+      if (cu < 256) used[cu >> 6] |= 1ull << (cu & 63);
+    }
+  }
+  unsigned cn = 0;
+  if (e - b < 256) {
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      if (~used[x]) {
+        cn = 64 * x + __ffsll((long long)~used[x]) - 1;
+        break;
+      }
+    }
+  } else {
+    cn = mex_slow(v, p, M, col, word, b, e);
+  }
+  rmax = max(rmax, rv + 1);
+  st_relaxed(&word[v], pack(p, rv + 1, cn));
+  return true;
+}
+
+inline size_t kw_bcr_smem(int R, unsigned pal) {
+  return (size_t)(3 * R + 2 + 4 * pal + 1) * sizeof(uint32_t);
+}
+
+__global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
+  __shared__ int s_halt;
+  if (threadIdx.x == 0) s_halt = V.halt ? ld_status(V.halt) : 0;
+  __syncthreads();
+  if (s_halt) return;
+  extern __shared__ uint32_t sm[];
+  const int R = V.R;
+  const unsigned pal = V.pal;
+  uint32_t* sbase = sm;             // R + 1
+  uint32_t* rp = sbase + R + 1;     // R + 1 right-half slot prefix at this level
+  uint32_t* smax = rp + R + 1;      // R deepest round in this block
+  uint32_t* hist = smax + R;        // pal this block's vertices per previous colour
+  uint32_t* offb = hist + pal;      // pal this block's offset inside each bucket
+  uint32_t* lcur = offb + pal;      // pal
+  uint32_t* start = lcur + pal;     // pal + 1 bucket starts
+  __shared__ unsigned s_old[1];
+  for (int r = threadIdx.x; r <= R; r += blockDim.x) sbase[r] = V.site_start[r];
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = true;
+  for (unsigned p = 1; p <= V.levels && ok; ++p) {
+    // right-half slots of every lattice at level p
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      const RepPlan pl = V.plan[r];
+      const uint32_t N = sbase[r + 1] - sbase[r];
+      uint32_t n = 0;
+      if (p <= pl.levels) {
+        const unsigned long long gsz = (unsigned long long)pl.g << p;
+        n = (uint32_t)(((unsigned long long)N + gsz - 1) / gsz *
+                       ((unsigned long long)pl.g << (p - 1)));
+      }
+      rp[r] = n;
+      smax[r] = 0;
+    }
+    for (unsigned c = threadIdx.x; c < pal; c += blockDim.x) {
+      hist[c] = 0;
+      lcur[c] = 0;
+    }
+    __syncthreads();
+    block_scan_excl(rp, R);
+    const uint32_t Rtot = rp[R];
+    if (Rtot == 0) break;
+    auto vertex_of = [&](uint32_t slot) -> uint32_t {
+      const int r = find_le(rp, R, slot);
+      const RepPlan pl = V.plan[r];
+      const uint32_t v = kw_vertex(slot - rp[r], pl.g << (p - 1), p, pl.magic);
+      return v < sbase[r + 1] - sbase[r] ? sbase[r] + v : kNone;
+    };
+    uint32_t* bc = V.bcnt + (size_t)p * pal;
+    // bucket sizes: block histograms, then one reservation per (block, colour)
+    for (uint32_t slot = gtid; slot < Rtot; slot += nth) {
+      const uint32_t gv = vertex_of(slot);
+      if (gv != kNone) atomicAdd(&hist[(uint32_t)(ld_relaxed(&V.word[gv]) & kColMask)], 1u);
+    }
+    __syncthreads();
+    for (unsigned c = threadIdx.x; c < pal; c += blockDim.x)
+      offb[c] = hist[c] ? atomicAdd(&bc[c], hist[c]) : 0u;
+    if (!grid_sync(V.bar, V.status, V.ns_limit)) {
+      ok = false;
+      break;
+    }
+    for (unsigned c = threadIdx.x; c < pal; c += blockDim.x) start[c] = ld_u32_gpu(&bc[c]);
+    __syncthreads();
+    block_scan_excl(start, (int)pal);
+    for (uint32_t slot = gtid; slot < Rtot; slot += nth) {
+      const uint32_t gv = vertex_of(slot);
+      if (gv == kNone) continue;
+      const uint32_t c = (uint32_t)(ld_relaxed(&V.word[gv]) & kColMask);
+      V.list[start[c] + offb[c] + atomicAdd(&lcur[c], 1u)] = gv;
+    }
+    if (!grid_sync(V.bar, V.status, V.ns_limit)) {
+      ok = false;
+      break;
+    }
+    // buckets from the largest previous colour down, one grid barrier apart.  Between its
+    // arrival at a barrier and its wait, each thread fetches the row of its first item of the
+    // next non-empty bucket (nothing there depends on the bucket being finished).
+    const unsigned long long t_start = global_ns();
+    auto next_bucket = [&](int c) {  // largest non-empty bucket below c, -1 if none
+      for (--c; c >= 0; --c)
+        if (start[c + 1] > start[c]) return c;
+      return -1;
+    };
+    int c = next_bucket((int)pal);
+    KwRow w;
+    w.gv = kNone;
+    if (c >= 0 && gtid < start[c + 1] - start[c])
+      kw_fetch(w, ld_u32_gpu(&V.list[start[c] + gtid]), V.row_ptr, V.col);
+    while (c >= 0 && ok) {
+      const uint32_t b0 = start[c], n = start[c + 1] - b0;
+      bool mine = true;
+      for (uint32_t q = gtid; q < n && mine; q += nth) {
+        if (q != gtid) kw_fetch(w, ld_u32_gpu(&V.list[b0 + q]), V.row_ptr, V.col);
+        const uint32_t gv = w.gv;
+        const int r = find_le(sbase, R, gv);
+        const uint32_t base = sbase[r];
+        unsigned rm = 0;
+        mine = kw_recolour(gv - base, (uint32_t)c, w, p, V.plan[r].magic, V.col, V.word + base,
+                           rm, V.status, t_start, V.ns_limit);
+        atomicMax(&smax[r], rm);
+      }
+      grid_arrive(V.bar, s_old);
+      const int cn = next_bucket(c);
+      w.gv = kNone;
+      if (cn >= 0 && gtid < start[cn + 1] - start[cn])
+        kw_fetch(w, ld_u32_gpu(&V.list[start[cn] + gtid]), V.row_ptr, V.col);
+      // false for every block once an error was reported (status read after the barrier)
+      ok = grid_wait(V.bar, s_old, V.status, V.ns_limit);
+      c = cn;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      if (smax[r]) atomicMax(&V.cnt[r].lev_rounds[p & 31], smax[r]);
+  }
+}
+
+}  // namespace
+}  // namespace sco

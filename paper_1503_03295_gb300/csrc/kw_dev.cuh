@@ -56,10 +56,9 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t u, unsigned long long M) {
 
 // Smallest colour in [0, g) not held by a ready same-group neighbour (mex <= degree).
 __device__ __noinline__ unsigned mex_slow(uint32_t v, unsigned p, unsigned long long M,
-                                          const uint32_t* __restrict__ row_ptr,
                                           const uint32_t* __restrict__ col,
-                                          const unsigned long long* word) {
-  const uint32_t b = row_ptr[v], e = row_ptr[v + 1];
+                                          const unsigned long long* word, uint32_t b,
+                                          uint32_t e) {
   const uint32_t grp = fdiv(v, M) >> p;
   for (unsigned c = 0;; ++c) {
     bool used = false;
@@ -143,11 +142,45 @@ __device__ __noinline__ uint32_t kw_attempt(uint32_t v, uint32_t cv, unsigned p,
       }
     }
   } else {
-    cn = mex_slow(v, p, M, row_ptr, col, word);
+    cn = mex_slow(v, p, M, col, word, b, e);
   }
   rmax = max(rmax, rv + 1);
   st_relaxed(&word[v], pack(p, rv + 1, cn));
   return kNone;
+}
+
+
+// Pending vertices (bits of pend) that may try now: those with no recorded blocker, and those
+// whose blocker has been recoloured at level p.  The blockers' words are loaded eight at a
+// time, back to back, so a pass over a thread's vertices costs a few memory latencies
+// rather than one per vertex.
+__device__ __forceinline__ unsigned kw_ready(unsigned pend, const uint32_t (&wt)[32],
+                                             const unsigned long long* word, unsigned p) {
+  unsigned ready = 0, todo = pend;
+  while (todo) {
+    int as[8];
+    unsigned long long wv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      as[k] = -1;
+      if (todo) {
+        as[k] = __ffs(todo) - 1;
+        todo &= todo - 1;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      wv[k] = 0;
+      if (as[k] >= 0) {
+        const uint32_t b = wt[as[k]];
+        wv[k] = b == kNone ? ((unsigned long long)p << 48) : ld_relaxed(&word[b]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (as[k] >= 0 && tag_of(wv[k]) == p) ready |= 1u << as[k];
+  }
+  return ready;
 }
 
 }  // namespace

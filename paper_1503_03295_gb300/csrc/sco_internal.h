@@ -28,6 +28,7 @@ struct DevCounters {
   int ovf_full;                     // the switch wrote more half-edges than the overflow list holds
   double acc[8];                    // observable accumulators
   unsigned int lev_rounds[32];      // deepest dependency chain per KW level
+  unsigned int bar[2];              // grid barrier of the persistent colouring kernel
 };
 
 // ---- scan.cu ----
@@ -100,6 +101,8 @@ struct ColourBufs {
   uint32_t* perm;    // N
   uint32_t* tile_cnt;  // palette x tiles (+1) per-tile colour counts, scanned in place
   uint64_t* scan_tmp;
+  uint32_t* bcnt;    // 32 x palette KW bucket sizes per level
+  uint32_t* meta;    // 6 words: one-lattice view of the persistent colouring kernel
 };
 constexpr uint32_t kMaxStablePalette = 12288;  // palettes up to this size get stable classes
 constexpr int64_t kClassTileSites = 2048;

@@ -79,12 +79,15 @@ def test_results_do_not_depend_on_tuning():
     ps = _mixed(sco.FP32_GUARDED)[:6]
     n = 9
     ref = sco.Batch(ps)
-    ref.set_tuning(steps_per_graph=1, sweep_blocks_per_sm=1, kw_blocks_per_sm=1, use_graph=0)
+    ref.set_tuning(steps_per_graph=1, sweep_blocks_per_sm=1, kw_blocks_per_sm=1, use_graph=0,
+                   kw_schedule=1)
     ref.run(n)
     want = [ref.spins(r) for r in range(len(ps))]
     for t in (dict(steps_per_graph=4, sweep_blocks_per_sm=2, kw_blocks_per_sm=2, use_graph=1),
               dict(steps_per_graph=3, sweep_blocks_per_sm=6, kw_blocks_per_sm=4, use_graph=1),
-              dict(steps_per_graph=1, sweep_blocks_per_sm=3, kw_blocks_per_sm=1, use_graph=0)):
+              dict(steps_per_graph=1, sweep_blocks_per_sm=3, kw_blocks_per_sm=1, use_graph=0),
+              dict(steps_per_graph=2, sweep_blocks_per_sm=4, kw_blocks_per_sm=2, use_graph=1,
+                   kw_schedule=1)):
         with sco.Batch(ps) as b:
             b.set_tuning(**t)
             b.run(4)
