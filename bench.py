@@ -50,7 +50,40 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--seq-steps", type=int, default=2,
                     help="steps per replica of the sequential single-lattice comparison")
+    ap.add_argument("--batch-sizes", default="64,128,256,512",
+                    help="lattice sizes of the batched arm (16 temperatures each by default)")
+    ap.add_argument("--batch-temps", type=int, default=16)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched arm: keep the default launch tuning")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run only the batched arm and print its object (profiling)")
     return ap.parse_args()
+
+
+def rank_seed(seed, rank):
+    """Seed of rank r's lattice: every rank runs an independent replica (no collective on
+    the data path)."""
+    return seed + rank
+
+
+def batch_seed_offset(rank):
+    """Added to every replica seed of the batched arm on rank r."""
+    return 1000 * rank
+
+
+def max_over_ranks(x, world, device=None):
+    """Max of a per-rank time over all ranks (the job's time); identity at world size 1."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(sites_per_rank, steps, world, ms):
+    """Spin updates per second of the whole job: every rank's sites, over the max time."""
+    return sites_per_rank * steps * world / (ms / 1e3)
 
 
 def dist_env():
@@ -122,6 +155,9 @@ class ClockSampler:
 
 
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal
+# DRAM bytes (read + write) of one FP64 sweep launch (one colour class) at L=2304, T=0.6D,
+# seed 0, from one ncu capture (profiles/dram_traffic_L2304_T0.6.md); valid for that workload
+SWEEP64_TRAFFIC_PER_CLASS = 73.3e6
 
 
 def algorithmic_bytes(k, M):
@@ -171,8 +207,8 @@ def run_ours(args, rank, world, local):
     N = L * L
 
     def lattice(prec):
-        return sco.Lattice(sco.make_params(L, T=args.T, seed=args.seed + rank, precision=prec),
-                           stream=sh)
+        return sco.Lattice(sco.make_params(L, T=args.T, seed=rank_seed(args.seed, rank),
+                                           precision=prec), stream=sh)
 
     def barrier():
         if world > 1:
@@ -200,18 +236,11 @@ def run_ours(args, rank, world, local):
         launches = lat.observables()["kernel_launches"] - l0
         return ms, ph, launches
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     out = {}
     lat = lattice(sco.FP64)
     with ClockSampler(local) as clk:
         ms, ph, launches = timed(lat, args.steps, args.warmup, timing=True)
-    ms = max_over_ranks(ms)
+    ms = max_over_ranks(ms, world, dev)
     obs = lat.observables()
     out["fp64"] = dict(ms=ms, phases=ph, launches=launches, obs=obs, clocks=clk.summary())
     if not args.no_e2e:
@@ -233,7 +262,7 @@ def run_ours(args, rank, world, local):
             assert Lb.sco_get_spins(lat.handle, C.c_void_p(hout.data_ptr()), 0) == 0
             hin, hout = hout, hin
         torch.cuda.synchronize(dev)
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
         out["e2e"] = dict(value=N * K * world / t_e2e, unit=UNIT, h2d_bytes_per_step=3 * N * 8,
                           d2h_bytes_per_step=3 * N * 8, steps=K)
     lat.close()
@@ -241,7 +270,7 @@ def run_ours(args, rank, world, local):
     if not args.no_fp32:
         lat32 = lattice(sco.FP32_GUARDED)
         ms32, ph32, l32 = timed(lat32, args.steps, args.warmup, timing=True)
-        ms32 = max_over_ranks(ms32)
+        ms32 = max_over_ranks(ms32, world, dev)
         out["fp32"] = dict(ms=ms32, phases=ph32, launches=l32, obs=lat32.observables())
         lat32.close()
         del lat32
@@ -259,12 +288,13 @@ def run_batch(args, rank, local):
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    ps = sco.replica_params(precision=sco.FP32_GUARDED)
+    sizes = tuple(int(x) for x in args.batch_sizes.split(","))
+    ps = sco.replica_params(L_list=sizes, n_T=args.batch_temps, precision=sco.FP32_GUARDED)
     for p in ps:
-        p.seed += 1000 * rank
+        p.seed += batch_seed_offset(rank)
     ntot = sum(p.Lx * p.Ly for p in ps)
     b = sco.Batch(ps, stream=stream.cuda_stream)
-    tuning = b.autotune(trial_steps=2)
+    tuning = b.tuning() if args.no_autotune else b.autotune(trial_steps=2)
     b.run(args.warmup)
     i0 = b.info()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -276,7 +306,8 @@ def run_batch(args, rank, local):
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
     i1 = b.info()
-    obs = [b.observables(r) for r in (0, 15, 48, 63)]
+    picks = sorted({0, args.batch_temps - 1, len(ps) - args.batch_temps, len(ps) - 1})
+    obs = [b.observables(r) for r in picks]
     b.close()
     del b
     # the same replicas as single lattices, one after another
@@ -301,11 +332,12 @@ def run_batch(args, rank, local):
     return {
         "value": value, "unit": UNIT, "ms_per_step": ms / args.batch_steps,
         "steps": args.batch_steps, "replicas": len(ps), "sites": ntot, "precision": "fp32_guarded",
-        "workload": "64 replicas: L in {64,128,256,512} x 16, T = (0.2 + b 1.3/15) D, seed r, "
-                    "J=0, D=1, n_sw=1",
+        "workload": "%d replicas: L in {%s} x %d, T = (0.2 + b 1.3/%d) D, seed r, J=0, D=1, "
+                    "n_sw=1" % (len(ps), args.batch_sizes, args.batch_temps,
+                                max(args.batch_temps - 1, 1)),
         "tuning": tuning, "gpu_launches": i1["launches"] - i0["launches"],
         "graph_launches": i1["graph_launches"] - i0["graph_launches"], "replans": i1["replans"],
-        "sample_max_degree": {str(r): o["max_degree"] for r, o in zip((0, 15, 48, 63), obs)},
+        "sample_max_degree": {str(r): o["max_degree"] for r, o in zip(picks, obs)},
         "sequential": {"value": seq_value, "ms_per_step_all_replicas": seq_ms / args.seq_steps,
                        "steps": args.seq_steps, "gpu_launches": seq_launches},
         "speedup_vs_sequential": value / seq_value,
@@ -334,13 +366,20 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.only_batch:
+        import torch
+        torch.cuda.set_device(local)
+        b = run_batch(args, rank, local)
+        if rank == 0:
+            print(json.dumps({"batched": b}), flush=True)
+        return
     res = run_ours(args, rank, world, local)
     if rank != 0:
         return
     N = args.L * args.L
     K = args.steps
     f64 = res["fp64"]
-    value = N * K * world / (f64["ms"] / 1e3)
+    value = whole_job_rate(N, K, world, f64["ms"])
     obs = f64["obs"]
     k = 2.0 * obs["n_edges"] / N
     levels = 0
@@ -354,9 +393,13 @@ def main():
     roof = rooflines(per_step, N, k, levels, cand, hbm, how, True)
     dom = max(per_step, key=per_step.get)
     if roof[dom].get("fp64_achieved_GFLOPs"):
+        traffic = None
+        if dom == "sweep" and args.L == 2304 and abs(args.T - 0.6) < 1e-9 and args.seed == 0:
+            traffic = SWEEP64_TRAFFIC_PER_CLASS * obs["n_colours"]  # bytes per step (all classes)
         primary = {"bound": "alu", "kernel": dom, "achieved": roof[dom]["fp64_achieved_GFLOPs"],
                    "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                   "frac": roof[dom]["fp64_frac"], "traffic": None,
+                   "frac": roof[dom]["fp64_frac"], "traffic": traffic,
+                   "traffic_unit": "DRAM bytes per step of the phase (ncu, full size)",
                    "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
                    "algorithmic_fp64_ops_per_update": roof[dom]["algorithmic_fp64_ops_per_update"]}
     else:
@@ -388,7 +431,7 @@ def main():
         f32 = res["fp32"]
         p32 = phase_ms(f32["phases"])
         line["fp32_guarded"] = {
-            "value": N * K * world / (f32["ms"] / 1e3), "ms_per_step": f32["ms"] / K,
+            "value": whole_job_rate(N, K, world, f32["ms"]), "ms_per_step": f32["ms"] / K,
             "gpu_launches": f32["launches"], "phases_ms_per_step": p32,
             "roofline_phases": rooflines(p32, N, k, levels, cand, hbm, how, False),
             "guard_hits_fp32": f32["obs"]["guard_hits_fp32"],

@@ -60,6 +60,9 @@ DevParams make_dev_params(const sco_params& p) {
   P.bD = P.beta * p.D;
   P.inv_bD58 = P.bD > 0.0 ? 0x1p58 / P.bD : 0.0;
   P.inv_bD58_f = (float)P.inv_bD58;
+  P.beta_f = (float)P.beta;
+  P.bJ_f = (float)(P.beta * P.J);
+  P.switching = P.bD > 0.0 ? 1 : 0;
   P.lx_magic = div_magic((unsigned long long)p.Lx);
   P.key0 = p.seed;
   P.key1 = (uint64_t)(uint32_t)p.replica;

@@ -22,6 +22,9 @@ struct DevParams {
   double J, D, beta, bD;  // beta = fl(1/T), bD = fl(beta * D)
   double inv_bD58;        // fl(2^58 / bD): exponential draw -> hazard prefix units
   float inv_bD58_f;       // its FP32 rounding
+  float beta_f;           // fl32(beta), for the FP32 screens (no FP64 operation there)
+  float bJ_f;             // fl32(fl(beta J))
+  int switching;          // 1 when beta D > 0 (pairs can be switched off)
   uint64_t key0, key1;    // Philox key: seed, replica
   double ln2_hi, ln2_lo;  // ln 2 as a double-double
   unsigned long long lx_magic;  // floor((2^64 - 1) / Lx) + 1 (0 when Lx = 1)

@@ -128,7 +128,7 @@ __device__ __forceinline__ int accept_fp32(const DevParams& P, const SiteCtx& c,
                                            const uint32_t* __restrict__ row_ptr,
                                            const uint32_t* __restrict__ col) {
   if (c.u < 0x1p-100) return 2;
-  const float beta = (float)P.beta;
+  const float beta = P.beta_f;
   const float ax = (float)c.S[0], ay = (float)c.S[1], az = (float)c.S[2];
   const float nx = (float)c.Sn[0], ny = (float)c.Sn[1], nz = (float)c.Sn[2];
   float sum = 0.f, comp = 0.f, sum_abs = 0.f, pz_o = 1.f, pz_n = 1.f, lin = 0.f, c0s = 0.f;
@@ -184,7 +184,7 @@ __device__ __forceinline__ int accept_fp32(const DevParams& P, const SiteCtx& c,
       h1 += s32[P.N + nb[q]];
       h2 += s32[2 * P.N + nb[q]];
     }
-    const float bj = (float)(P.beta * P.J);
+    const float bj = P.bJ_f;
     tex = -bj * ((nx - ax) * h0 + (ny - ay) * h1 + (nz - az) * h2);
     bex = 0x1p-14f * fabsf(bj);
   }

@@ -74,7 +74,7 @@ __device__ __noinline__ int64_t next_candidate_dd(const DevParams& P, const Near
 __device__ __forceinline__ int64_t next_candidate(const DevParams& P, const NearTable& T,
                                                   int64_t s, uint64_t Ws, uint64_t Wtot,
                                                   uint64_t wE, unsigned& ghits) {
-  if (s >= T.K - 1 || !(P.bD > 0.0)) return T.K;
+  if (s >= T.K - 1 || !P.switching) return T.K;
   const double up = u53pos(wE);
   const double tau = -log(up) * P.inv_bD58;
   const uint64_t rem = Wtot - Ws;
@@ -113,7 +113,7 @@ __device__ __forceinline__ int64_t next_candidate_fp32(const DevParams& P, const
                                                        int64_t s, uint64_t Ws, uint64_t Wtot,
                                                        uint64_t wE, unsigned& g32,
                                                        unsigned& ghits) {
-  if (s >= T.K - 1 || !(P.bD > 0.0)) return T.K;
+  if (s >= T.K - 1 || !P.switching) return T.K;
   const uint64_t m53 = wE >> 11;  // u+ = (m53 + 1) 2^-53
   float E;
   if (m53 >= (1ull << 52)) {
@@ -193,7 +193,7 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32, do
   const float pa = Si32[0] * fx + Si32[1] * fy;
   const float pb = Sj32[0] * fx + Sj32[1] * fy;
   const float V = t32.x * (fr2 * ss - 3.0f * (pa * pb));
-  const float beta = (float)P.beta;
+  const float beta = P.beta_f;
   const float b = beta * (V - t32.y);
   const float pr = -expm1f(b);
   const float q = t32.w;  // fl32 of the FP64 q: 2^-24 on top of its 4 ulp
