@@ -235,6 +235,17 @@ sco_status sco_batch_info(sco_batch* b, int64_t* total_sites, int64_t* steps_don
 /* Waits for the batch's stream; returns the sticky device status. */
 sco_status sco_batch_sync(sco_batch* b);
 
+/* Self-test of the library's own elementary function: the branch-free expm1 for x <= 0.35 used
+ * by the FP64 decisions of the switch and the sweep (argument reduction by ln 2, a degree-8
+ * polynomial on |r| <= 0.35, -1 below x = -40), stated relative error bound 2^-42, which those
+ * decisions carry in their error bounds.  Evaluates it at n >= 17 points of [-50, 0.35] (16
+ * fixed points, then Philox-jittered evenly spaced ones from `seed`) and returns the largest
+ * relative error against the library's double-double expm1 (max_rel_err) and against CUDA's
+ * expm1 (max_rel_diff_cuda, may be NULL).  Synchronous; uses the current device.  There is no
+ * counterpart in the paper. */
+sco_status sco_selftest_expm1(int64_t n, uint64_t seed, double* max_rel_err,
+                              double* max_rel_diff_cuda);
+
 /* Waits for the context's stream; returns the sticky device status. */
 sco_status sco_sync(sco_ctx* c);
 

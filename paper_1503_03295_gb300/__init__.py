@@ -106,6 +106,8 @@ def load():
         "sco_batch_info": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                             C.POINTER(C.c_int64), C.POINTER(C.c_int32)], st),
         "sco_batch_sync": ([vp], st),
+        "sco_selftest_expm1": ([C.c_int64, C.c_uint64, C.POINTER(C.c_double),
+                                C.POINTER(C.c_double)], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -140,6 +142,15 @@ def kw_colour_static(row_ptr_dev, col_dev, n, colour_dev, variant=0, stream=None
                                        C.byref(r), C.c_void_p(stream or 0)),
            "sco_kw_colour_static")
     return d.value, r.value
+
+
+def selftest_expm1(n=1 << 24, seed=1):
+    """Largest relative error of the library's expm1 (x <= 0.35) against double-double and
+    against CUDA's expm1 (see sco_selftest_expm1)."""
+    a, b = C.c_double(), C.c_double()
+    _check(load().sco_selftest_expm1(int(n), int(seed), C.byref(a), C.byref(b)),
+           "sco_selftest_expm1")
+    return a.value, b.value
 
 
 def make_params(Lx, Ly=None, T=1.0, D=1.0, J=0.0, seed=0, n_sw=1, precision=FP64,

@@ -27,7 +27,7 @@ struct RepDesc {
   const double2* xy;
   const double* xyq;
   const float4* xy32;
-  const double4_32a* sw64;
+  const Sw64* sw64;
   const float4* sw32;
   int32_t mnn0, mnn1;  // list index of the displacements (1, 0) and (0, 1)
   uint32_t base;       // first global site

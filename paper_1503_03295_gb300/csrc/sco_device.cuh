@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "expm1_poly.h"
+
 namespace sco {
 
 // Philox counter word 3 per use of the random stream (the library's stream layout).
@@ -123,6 +125,54 @@ __device__ __forceinline__ double pair_V(double Dc, double r2, double ax, double
   const double pa = ax * fx + ay * fy;
   const double pb = bx * fx + by * fy;
   return Dc * (r2 * ss - 3.0 * (pa * pb));
+}
+
+// The library's own expm1 for x <= 0.35, branch-free (a warp never runs two versions): x =
+// k ln2 + r with k = round(x / ln2) (by the 1.5 2^52 shift) and r = fma(-k, ln2, x),
+// expm1(r) = r p(r) (p of expm1_poly.h, interpolation error < 1e-13), expm1(x) =
+// fma(2^k, expm1(r), 2^k - 1), and -1 below x = -40 (e^x < 2^-57).  Relative error below
+// 2^-43: interpolation 2^-43.2; Horner <= gamma_16 p(|r|) / p(r) <= 23 u; r off by at most
+// |k| |ln2 - fl(ln2)| <= 58 x 2.3e-17; for k <= -1 the 2^k expm1(r) part (<= 0.42 2^k) carries
+// these while |expm1(x)| >= 0.29.  Stated as kExpm1RelErr = 2^-42; the FP64 decisions carry it
+// in their error bounds.
+constexpr double kExpm1RelErr = 0x1p-42;
+__device__ __forceinline__ double expm1_np(double x) {
+  const double t = fma(x, kExpInvLn2, 0x1.8p52);
+  const double kd = t - 0x1.8p52;
+  const int k = max(__double2loint(t), -1000);
+  const double r = fma(-kd, kExpLn2, x);
+  const double e = r * expm1_poly(r);
+  const double s = __longlong_as_double((long long)(1023 + k) << 52);
+  const double res = fma(s, e, s - 1.0);
+  // x < -40 from the bits: sign set and |x| bits above those of 40
+  const long long xb = __double_as_longlong(x);
+  return (xb < 0 && (xb & 0x7FFFFFFFFFFFFFFFll) > 0x4044000000000000ll) ? -1.0 : res;
+}
+
+// Sweep constants of a pair at (|dx|, |dy|) for the FP64 decisions (64 bytes).  With the
+// signs of (dx, dy) applied to a3x, a3y, ax, ay, the field of S_j on site i scaled by beta is
+// f = a1 S_j - (S_j . (a3x, a3y)) (dx, dy, 0), so x = beta (V - Vmax) = S_i . f - bvm.
+struct __align__(64) Sw64 {
+  double a1;        // fl(beta fl(Dc r^2))
+  double a3x, a3y;  // fl(fl(beta fl(3 Dc)) |dx|), fl(fl(beta fl(3 Dc)) |dy|)
+  double ax, ay;    // |dx|, |dy|
+  double bvm;       // fl(beta Vmax)
+  double c0;        // bound on |error of x| not scaling with |x|, plus 2^-52 (2 beta Vmax)
+  double pad;
+};
+
+// x with its sign flipped when neg (bit operation, no FP64 instruction)
+__device__ __forceinline__ double flip_if(double x, bool neg) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
+}
+// x < 0 strictly (not -0), from the bits
+__device__ __forceinline__ bool neg_strict(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 && b != (long long)0x8000000000000000ull;
+}
+// bits of a double >= 0, ordered like its value
+__device__ __forceinline__ unsigned long long pos_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
 }
 
 // ---------------------------------------------------------------------------------------

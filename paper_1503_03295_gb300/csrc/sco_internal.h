@@ -46,7 +46,7 @@ struct Table {
   double2* xy = nullptr;     // by (|dx|, |dy|): {fl(D c(r^2)), V_max = fl(fl(D A) 2^-59)}
   double* xyq = nullptr;     // by (|dx|, |dy|): q = -expm1(-2 beta V_max), candidate probability
   float4* xy32 = nullptr;    // by (|dx|, |dy|): FP32 copies {Dc, Vmax, 2 beta Vmax, q}
-  double4_32a* sw64 = nullptr;   // sweep, by (|dx|, |dy|): {fl(Dc r^2), fl(3 Dc), fl(beta Vmax), c0}
+  Sw64* sw64 = nullptr;      // sweep, by (|dx|, |dy|): FP64 decision constants (see Sw64)
   float4* sw32 = nullptr;    // the same in FP32 (with its own c0)
   int32_t m_nn[2] = {-1, -1};
 };

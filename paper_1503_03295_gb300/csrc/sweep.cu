@@ -14,7 +14,7 @@ namespace {
 // appended to the deferred list of the colour and settled by k_resolve (one warp per site),
 // so that no thread of this kernel runs the long FP64 / double-double evaluations.
 template <int PREC>
-__global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) k_sweep(const DevParams P, const double4_32a* __restrict__ sw,
+__global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) k_sweep(const DevParams P, const Sw64* __restrict__ sw,
                                                const float4* __restrict__ sw32,
                                                double* __restrict__ s, float* __restrict__ s32,
                                                const uint32_t* __restrict__ row_ptr,
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) k_sweep(const DevParam
 }
 
 // Settles the deferred sites of a colour: one warp per site, FP64 then double-double.
-__global__ void __launch_bounds__(128) k_resolve(const DevParams P, const double4_32a* __restrict__ sw,
+__global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* __restrict__ sw,
                                                  double* __restrict__ s, float* __restrict__ s32,
                                                  const uint32_t* __restrict__ row_ptr,
                                                  const uint32_t* __restrict__ col,

@@ -33,27 +33,32 @@ struct SiteCtx {
 constexpr int kScale64 = 600;
 constexpr int kScale32 = 60;
 
-// Pair field on site i from the sweep table entry {A1, A3, beta Vmax, c0}:
-// f = A1 S_j - A3 (S_j.d) d, V(S) = S.f, x = beta V - beta Vmax.
+// Pair terms from the sweep table entry (Sw64): the beta-scaled field of S_j on site i,
+// f = a1 S_j - (S_j . a3 d) d, gives x = S.f - bvm = beta V(S) - beta Vmax for the old and the
+// new spin.
 //
 // Error bound of the margin mu = ln u + beta dE' (first order, doubled):
-//   per pair, |dx| <= c0 + eps_r |x| (c0 from the table covers |dV| and fl(beta Vmax));
-//   z = -expm1(x) has relative error eps_f + |dx| / z;  log of a product of n factors adds
-//   n eps_r;  log itself eps_f |log P|;  beta sum (V' - V) adds 2 sum c0 + (n + 2) eps_r |.|.
-// With zmin = min z and xmax = max |x|, sum_j |dx_j| / z_j <= (sum c0 + n eps_r xmax) / zmin,
-// which must stay below 2^-10 (first order) or the decision is left undecided.
+//   per pair, |dx| <= c0 + eps_r |x|, and c0 from the table already includes eps_r 2 beta Vmax;
+//   z = -expm1(x) has relative error eps_z + |dx| / z;  log of a product of n factors adds
+//   n eps_r;  the logarithms eps_f |log P|;  sum (x_new - x_old) adds 2 sum c0 (the x errors)
+//   and (n + 2) eps_r sum |x_new - x_old| <= (n + 2) eps_r 2 sum bvm <= (n + 2) sum c0 (c0 >=
+//   2^-51 bvm by construction).  With zmin = min z, sum_j |dx_j| / z_j <= sum c0 / zmin, which
+//   must stay below 2^-10 (first order) or the decision is left undecided.
 
 // FP64 decision (0: reject, 1: accept, 2: undecided).  eps_r = 2^-52 (unit roundoff, with
-// margin), eps_f = 2^-50 (expm1 / log within 4 ulp).
+// margin), eps_f = 2^-50 for the CUDA logarithms (within 4 ulp), eps_z = kExpm1RelErr for the
+// library's expm1_np (two per pair, doubled: 4 eps_z).  Compares, minima and renormalisation
+// tests work on the bits of positive doubles (integer pipe).
 __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
-                                           const double4_32a* __restrict__ sw,
+                                           const Sw64* __restrict__ sw,
                                            const double* __restrict__ s,
                                            const uint32_t* __restrict__ row_ptr,
                                            const uint32_t* __restrict__ col) {
-  const double beta = P.beta;
   const double S0 = c.S[0], S1 = c.S[1], S2 = c.S[2];
   const double N0 = c.Sn[0], N1 = c.Sn[1], N2 = c.Sn[2];
-  double sdv = 0.0, sdv_abs = 0.0, pz_o = 1.0, pz_n = 1.0, zmin = 1.0, xmax = 0.0, c0s = 0.0;
+  double bdv = 0.0, pz_o = 1.0, pz_n = 1.0, c0s = 0.0;
+  unsigned long long zmin_b = pos_bits(1.0);
+  const unsigned long long small_b = pos_bits(0x1p-600);
   int sc_o = 0, sc_n = 0, n = 0;
   const uint32_t e1 = row_ptr[c.i + 1];
   for (uint32_t e = row_ptr[c.i]; e < e1; ++e) {
@@ -63,31 +68,29 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     const uint32_t yj = site_row((uint32_t)j, P);
     const int32_t dx = (int32_t)((uint32_t)j - yj * (uint32_t)P.Lx) - c.xi;
     const int32_t dy = (int32_t)yj - c.yi;
-    const double4_32a t = sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
-    const double fx = (double)dx, fy = (double)dy;
+    const Sw64& t = sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
+    const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
+    const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
+    const double a1 = t.a1, bvm = t.bvm;
     const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
-    const double tp = t.y * (bx * fx + by * fy);
-    const double gx = t.x * bx - tp * fx;
-    const double gy = t.x * by - tp * fy;
-    const double gz = t.x * bz;
-    const double Vn = N0 * gx + N1 * gy + N2 * gz;
-    const double Vo = S0 * gx + S1 * gy + S2 * gz;
-    const double xn = beta * Vn - t.z, xo = beta * Vo - t.z;
-    if (!(xn < 0.0) || !(xo < 0.0)) return 2;
-    const double zn = -expm1(xn), zo = -expm1(xo);
+    const double tp = bx * ax3 + by * ay3;
+    const double gx = a1 * bx - tp * fx;
+    const double gy = a1 * by - tp * fy;
+    const double gz = a1 * bz;
+    const double xn = (N0 * gx + N1 * gy + N2 * gz) - bvm;
+    const double xo = (S0 * gx + S1 * gy + S2 * gz) - bvm;
+    if (!neg_strict(xn) || !neg_strict(xo)) return 2;
+    const double zn = -expm1_np(xn), zo = -expm1_np(xo);
     pz_n *= zn;
     pz_o *= zo;
-    if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
-    if (pz_o < 0x1p-600) { pz_o *= 0x1p600; ++sc_o; }
-    const double dv = Vn - Vo;
-    sdv += dv;
-    sdv_abs += fabs(dv);
-    zmin = fmin(zmin, fmin(zn, zo));
-    xmax = fmax(xmax, fmax(-xn, -xo));
-    c0s += t.w;
+    if (pos_bits(pz_n) < small_b) { pz_n *= 0x1p600; ++sc_n; }
+    if (pos_bits(pz_o) < small_b) { pz_o *= 0x1p600; ++sc_o; }
+    bdv += xn - xo;
+    zmin_b = min(zmin_b, min(pos_bits(zn), pos_bits(zo)));
+    c0s += t.c0;
     ++n;
   }
-  const double lin = n > 0 ? (c0s + n * 0x1p-52 * xmax) / zmin : 0.0;
+  const double lin = n > 0 ? c0s / __longlong_as_double((long long)zmin_b) : 0.0;
   if (!(lin <= 0x1p-10)) return 2;
   double tex = 0.0, bex = 0.0;
   if (P.J != 0.0) {
@@ -102,18 +105,17 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
       h2 += s[2 * P.N + nb[q]];
     }
     const double dot = (c.Sn[0] - c.S[0]) * h0 + (c.Sn[1] - c.S[1]) * h1 + (c.Sn[2] - c.S[2]) * h2;
-    tex = -(beta * P.J) * dot;
-    bex = 0x1p-44 * fabs(beta * P.J);
+    tex = -(P.beta * P.J) * dot;
+    bex = 0x1p-44 * fabs(P.beta * P.J);
   }
   const double lo = log(pz_o), ln = log(pz_n);
   // prod z = stored product * 2^(-kScale * count)
   const double scale = (double)((sc_n - sc_o) * kScale64) * P.ln2_hi;
   const double lu = log(c.u);
-  const double bdv = beta * sdv;
   const double mu = lu + ((bdv + tex) + ((lo - ln) + scale));
-  const double B = 2.0 * (2.0 * c0s + (double)(n + 2) * 0x1p-52 * beta * sdv_abs + 2.0 * lin +
-                          n * (0x1p-48 + 0x1p-51) + 0x1p-50 * (fabs(lo) + fabs(ln) + fabs(lu)) +
-                          bex + 0x1p-51 * (fabs(scale) + fabs(tex) + fabs(bdv) + fabs(mu)));
+  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr + 0x1p-51) +
+                          0x1p-50 * (fabs(lo) + fabs(ln) + fabs(lu)) + bex +
+                          0x1p-51 * (fabs(scale) + fabs(tex) + fabs(bdv) + fabs(mu)));
   if (mu < -B) return 1;
   if (mu > B) return 0;
   return 2;
@@ -266,14 +268,14 @@ __device__ __forceinline__ dd warp_sum_dd(dd v) {
 }
 
 // The FP64 decision of accept_fp64 with the pairs of the site spread over the 32 lanes of a
-// warp (partial sums, products taken to logarithms per lane, then reduced).  Same bound.
+// warp (partial sums, products taken to logarithms per lane, then reduced).  Same bound, plus
+// the per-lane logarithms.
 __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
-                                const double4_32a* __restrict__ sw,
+                                const Sw64* __restrict__ sw,
                                 const double* __restrict__ s,
                                 const uint32_t* __restrict__ row_ptr,
                                 const uint32_t* __restrict__ col, int lane) {
-  const double beta = P.beta;
-  double sdv = 0.0, sdv_abs = 0.0, pz_o = 1.0, pz_n = 1.0, zmin = 1.0, xmax = 0.0, c0s = 0.0;
+  double bdv = 0.0, pz_o = 1.0, pz_n = 1.0, zmin = 1.0, c0s = 0.0;
   int sc_o = 0, sc_n = 0, n = 0, bad = 0;
   const uint32_t e1 = row_ptr[c.i + 1];
   for (uint32_t e = row_ptr[c.i] + lane; e < e1; e += 32) {
@@ -283,31 +285,28 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
     const uint32_t yj = site_row(j, P);
     const int32_t dx = (int32_t)(j - yj * (uint32_t)P.Lx) - c.xi;
     const int32_t dy = (int32_t)yj - c.yi;
-    const double4_32a t = sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
-    const double fx = (double)dx, fy = (double)dy;
+    const Sw64& t = sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
+    const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
+    const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
     const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
-    const double tp = t.y * (bx * fx + by * fy);
-    const double gx = t.x * bx - tp * fx;
-    const double gy = t.x * by - tp * fy;
-    const double gz = t.x * bz;
-    const double Vn = c.Sn[0] * gx + c.Sn[1] * gy + c.Sn[2] * gz;
-    const double Vo = c.S[0] * gx + c.S[1] * gy + c.S[2] * gz;
-    const double xn = beta * Vn - t.z, xo = beta * Vo - t.z;
-    if (!(xn < 0.0) || !(xo < 0.0)) {
+    const double tp = bx * ax3 + by * ay3;
+    const double gx = t.a1 * bx - tp * fx;
+    const double gy = t.a1 * by - tp * fy;
+    const double gz = t.a1 * bz;
+    const double xn = (c.Sn[0] * gx + c.Sn[1] * gy + c.Sn[2] * gz) - t.bvm;
+    const double xo = (c.S[0] * gx + c.S[1] * gy + c.S[2] * gz) - t.bvm;
+    if (!neg_strict(xn) || !neg_strict(xo)) {
       bad = 1;
       continue;
     }
-    const double zn = -expm1(xn), zo = -expm1(xo);
+    const double zn = -expm1_np(xn), zo = -expm1_np(xo);
     pz_n *= zn;
     pz_o *= zo;
     if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
     if (pz_o < 0x1p-600) { pz_o *= 0x1p600; ++sc_o; }
-    const double dv = Vn - Vo;
-    sdv += dv;
-    sdv_abs += fabs(dv);
+    bdv += xn - xo;
     zmin = fmin(zmin, fmin(zn, zo));
-    xmax = fmax(xmax, fmax(-xn, -xo));
-    c0s += t.w;
+    c0s += t.c0;
     ++n;
   }
   // per lane: log of its products, with the renormalisation folded in
@@ -315,15 +314,13 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
   const double ln = log(pz_n) - (double)(sc_n * kScale64) * P.ln2_hi;
   const double lsum = warp_sum_d(lo - ln);
   const double labs = warp_sum_d(fabs(lo) + fabs(ln));
-  sdv = warp_sum_d(sdv);
-  sdv_abs = warp_sum_d(sdv_abs);
+  bdv = warp_sum_d(bdv);
   c0s = warp_sum_d(c0s);
   zmin = warp_min_d(zmin);
-  xmax = warp_max_d(xmax);
   n = __reduce_add_sync(0xffffffffu, n);
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (bad) return 2;
-  const double lin = n > 0 ? (c0s + n * 0x1p-52 * xmax) / zmin : 0.0;
+  const double lin = n > 0 ? c0s / zmin : 0.0;
   if (!(lin <= 0x1p-10)) return 2;
   double tex = 0.0, bex = 0.0;
   if (P.J != 0.0) {
@@ -338,15 +335,14 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
       h2 += s[2 * P.N + nb[q]];
     }
     const double dot = (c.Sn[0] - c.S[0]) * h0 + (c.Sn[1] - c.S[1]) * h1 + (c.Sn[2] - c.S[2]) * h2;
-    tex = -(beta * P.J) * dot;
-    bex = 0x1p-44 * fabs(beta * P.J);
+    tex = -(P.beta * P.J) * dot;
+    bex = 0x1p-44 * fabs(P.beta * P.J);
   }
   const double lu = log(c.u);
-  const double bdv = beta * sdv;
   const double mu = lu + ((bdv + tex) + lsum);
-  const double B = 2.0 * (2.0 * c0s + (double)(n + 2) * 0x1p-52 * beta * sdv_abs + 2.0 * lin +
-                          n * (0x1p-48 + 0x1p-51) + 0x1p-50 * (labs + fabs(lu)) + 0x1p-49 * labs +
-                          bex + 0x1p-51 * (fabs(tex) + fabs(bdv) + fabs(mu)));
+  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr + 0x1p-51) +
+                          0x1p-50 * (labs + fabs(lu)) + 0x1p-49 * labs + bex +
+                          0x1p-51 * (fabs(tex) + fabs(bdv) + fabs(mu)));
   if (mu < -B) return 1;
   if (mu > B) return 0;
   return 2;

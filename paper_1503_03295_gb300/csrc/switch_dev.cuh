@@ -158,7 +158,8 @@ __device__ __noinline__ bool survives_dd(const DevParams& P, const double* Si, c
 }
 
 // FP64 survival test with its error bound: |dV| <= 2^-47 Dc r^2, fl(Vmax) within 2^-52,
-// expm1 within 4 ulp, so 1 - P and q within the terms below (doubled for margin).
+// the library's expm1_np within kExpm1RelErr (1 - P), the table's q (CUDA expm1) within 4 ulp, so
+// 1 - P and q within the terms below (doubled for margin).
 __device__ __forceinline__ bool survives_fp64(const DevParams& P, double Dc, double Vm, double q,
                                               double r2, const double* Si, const double* Sj,
                                               int32_t dx, int32_t dy, uint64_t A, double u1,
@@ -166,11 +167,12 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, double Dc, dou
   const double V = pair_V(Dc, r2, Si[0], Si[1], Si[2], Sj[0], Sj[1], Sj[2], (double)dx,
                           (double)dy);
   const double b = P.beta * (V - Vm);
-  const double pr = -expm1(b);  // q = -expm1(-fl(2 beta Vmax)) comes from the table
+  const double pr = -expm1_np(b);  // q = -expm1(-fl(2 beta Vmax)) comes from the table
   const double mu = pr - u1 * q;
   const double dV = 0x1p-47 * Dc * r2;
   const double B =
-      2.0 * (P.beta * (dV + 0x1p-52 * Vm) + 0x1p-52 * fabs(b) + 0x1p-49 * (fabs(pr) + q));
+      2.0 * (P.beta * (dV + 0x1p-52 * Vm) + 0x1p-52 * fabs(b) + 2.0 * kExpm1RelErr * fabs(pr) +
+             0x1p-49 * q);
   if (mu > B) return true;
   if (mu < -B) return false;
   ++ghits;

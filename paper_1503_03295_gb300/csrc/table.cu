@@ -67,13 +67,16 @@ __global__ void k_hazard(int64_t K, const uint32_t* __restrict__ disp, uint64_t*
   A[m] = hazard_A((int64_t)dx * dx + (int64_t)dy * dy);
 }
 
-// Sweep constants of a pair at (|dx|, |dy|): the field of S_j on site i is
-// f = A1 S_j - A3 (S_j.d) d with A1 = fl(Dc r^2), A3 = fl(3 Dc), so V(S) = S.f and
-// x = beta V - fl(beta Vmax).  c0 bounds the part of |x error| that does not scale with |x|:
-// FP64 |dV| <= 2^-46 Dc r^2, FP32 |dV| <= 2^-16 Dc r^2 (shadow spins, FP32 constants).
+// Sweep constants of a pair at (|dx|, |dy|).  FP64 (Sw64): the field of S_j on site i scaled
+// by beta, f = a1 S_j - (S_j . a3 d) d with a1 = fl(beta fl(Dc r^2)) and a3 d = fl(beta fl(3 Dc)) d,
+// so x = beta V - fl(beta Vmax) = S_i . f - bvm; c0 bounds the part of |x error| that does not
+// scale with |x|: |beta dV| <= 2^-46 beta Dc r^2 (FP64 products, the rounded beta-scaled
+// constants) plus 2^-51 beta Vmax (fl(beta Vmax)), plus 2^-52 (2 beta Vmax) for the rounding of
+// x itself (|x| <= 2 beta Vmax).  FP32 (float4 {A1, A3, beta Vmax, c0}): V(S) = S.f with
+// f = A1 S_j - A3 (S_j.d) d, |dV| <= 2^-16 Dc r^2 (shadow spins, FP32 constants).
 __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __restrict__ xy,
                      double* __restrict__ xyq, float4* __restrict__ xy32,
-                     double4_32a* __restrict__ sw64, float4* __restrict__ sw32) {
+                     Sw64* __restrict__ sw64, float4* __restrict__ sw32) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= (int64_t)Lx * Ly) return;
   const int64_t ax = q % Lx, ay = q / Lx;
@@ -89,9 +92,19 @@ __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __r
   xyq[q] = cq;
   xy32[q] = make_float4((float)dc, (float)vm, (float)a, (float)cq);
   const double a1 = dc * (double)r2, a3 = 3.0 * dc, bvm = beta * vm;
-  const double c64 = beta * (0x1p-46 * dc * (double)r2) + 0x1p-51 * bvm;
+  const double a3b = beta * a3;
+  const double c64 = beta * (0x1p-46 * dc * (double)r2) + 0x1p-51 * bvm + 0x1p-52 * (2.0 * bvm);
+  Sw64 t;
+  t.a1 = beta * a1;
+  t.a3x = a3b * (double)ax;
+  t.a3y = a3b * (double)ay;
+  t.ax = (double)ax;
+  t.ay = (double)ay;
+  t.bvm = bvm;
+  t.c0 = c64 * (1.0 + 0x1p-20);
+  t.pad = 0.0;
+  sw64[q] = t;
   const double c32 = beta * (0x1p-16 * dc * (double)r2) + 0x1p-21 * bvm;
-  sw64[q] = make_double4_32a(a1, a3, bvm, c64 * (1.0 + 0x1p-20));
   sw32[q] = make_float4((float)a1, (float)a3, (float)bvm, (float)(c32 * (1.0 + 0x1p-20)));
 }
 
@@ -103,7 +116,7 @@ cudaError_t table_build_xy(const DevParams& P, Table& t, cudaStream_t s, int64_t
   if ((e = cudaMalloc(&t.xy, nxy * sizeof(double2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&t.xy32, nxy * sizeof(float4))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&t.xyq, nxy * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&t.sw64, nxy * sizeof(double4_32a))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&t.sw64, nxy * sizeof(Sw64))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&t.sw32, nxy * sizeof(float4))) != cudaSuccess) return e;
   k_xy<<<(unsigned)((nxy + 255) / 256), 256, 0, s>>>(P.Lx, P.Ly, P.D, P.beta, t.xy, t.xyq,
                                                       t.xy32, t.sw64, t.sw32);

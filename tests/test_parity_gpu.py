@@ -181,3 +181,13 @@ def test_full_size_first_sweep_L2304():
     og, oo = g.observables(), o.observables()
     assert og["kw_rounds"] == oo["kw_rounds"]
     _same_energy(og["e_switched"], oo["e_switched"], g.N)
+
+
+def test_library_expm1_within_its_bound():
+    """The FP64 decisions take expm1 from the library's own branch-free implementation with a
+    stated relative error bound of 2^-42 (carried in their error bounds); check it against
+    double-double on 16M points of [-50, 0.35] (range ends, the -40 cut, reduction boundaries
+    included)."""
+    err, diff = sco.selftest_expm1(1 << 24, seed=3)
+    assert err < 2.0 ** -42
+    assert diff < 2.0 ** -42
