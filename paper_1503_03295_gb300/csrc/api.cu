@@ -108,6 +108,7 @@ struct sco_ctx {
   uint32_t cls_cap = 0;  // capacity of hist / off / cursor
   uint8_t* acc = nullptr;
   uint32_t* defer = nullptr;  // N sites whose decision goes to the warp-parallel resolve
+  double4_32a* prop = nullptr;  // N proposals {S', u} of the current MC step
   DevCounters* cnt = nullptr;   // device
   DevCounters* hcnt = nullptr;  // pinned mirror
   int64_t t = 0;
@@ -302,6 +303,7 @@ void free_all(sco_ctx* c) {
   cudaFree(c->cb.meta);
   cudaFree(c->acc);
   cudaFree(c->defer);
+  cudaFree(c->prop);
   cudaFree(c->cnt);
   if (c->hcnt) cudaFreeHost(c->hcnt);
   for (auto& e : c->evs) {
@@ -369,6 +371,7 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.meta, 8 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->acc, N);
   if (e == cudaSuccess) e = cudaMalloc(&c->defer, N * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&c->prop, N * sizeof(double4_32a));
   if (e == cudaSuccess) e = cudaMalloc(&c->cnt, sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMallocHost(&c->hcnt, sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, sizeof(DevCounters), c->st);
@@ -419,7 +422,7 @@ sco_status sco_sweep(sco_ctx* c, int32_t n_mcs) {
       PhaseTimer tm(c, kPhSweep);
       SCO_TRY(sweep_run(c->P, c->tab, c->s, c->s32, c->row_ptr, c->col, c->cb.perm, c->cb.off,
                         c->g, (uint64_t)c->t, c->p.precision, c->acc, c->defer, c->cb.dcnt,
-                        c->cnt, c->st, &c->launches));
+                        c->prop, c->cnt, c->st, &c->launches));
     }
     c->t++;
   }

@@ -456,6 +456,21 @@ __global__ void __launch_bounds__(32) kb_tile_scatter(const BatchDev B) {
 
 // ---- step (3): the colour-class sweep, one persistent kernel per MC step ----------------
 
+// Proposals of every site of every replica for this MC step (see take_proposal).
+__global__ void __launch_bounds__(256) kb_propose(const BatchDev B) {
+  if (block_halted(B)) return;
+  const int r = block_replica(B);
+  const RepDesc* d = B.desc + r;
+  const uint32_t base = B.site_start[r], N = B.site_start[r + 1] - base;
+  const uint32_t i = (blockIdx.x - B.blk_start[r]) * kBatchBlock + threadIdx.x;
+  if (i >= N) return;
+  SiteCtx c;
+  c.i = i;
+  const bool ok = propose(d->P, c, B.ctl->step);
+  B.prop[base + i] = ok ? make_double4_32a(c.Sn[0], c.Sn[1], c.Sn[2], c.u)
+                        : make_double4_32a(0.0, 0.0, 1.0, -1.0);
+}
+
 // Sites of class c (all replicas) one per thread; undecided ones go to the deferred list of
 // the colour; after a grid barrier one warp per deferred site settles it (FP64, then
 // double-double); a second barrier closes the colour.
@@ -473,7 +488,6 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) kb_sweep(const BatchDe
     sg2[r] = 0;
   }
   __syncthreads();
-  const uint64_t step = B.ctl->step;
   const uint32_t gmax = B.ctl->gmax;
   const uint32_t nth = gridDim.x * blockDim.x;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -492,7 +506,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) kb_sweep(const BatchDe
       float* s32 = B.s32 + so;
       SiteCtx x;
       load_site(P, x, gs - base, s);
-      if (!propose(P, x, step)) {
+      if (!take_proposal(x, B.prop + base)) {
         B.acc[gs] = 0;
         continue;
       }
@@ -522,7 +536,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) kb_sweep(const BatchDe
       float* s32 = B.s32 + so;
       SiteCtx x;
       load_site(P, x, gs - base, s);
-      propose(P, x, step);  // the same proposal (a pure function of (seed, i, t))
+      take_proposal(x, B.prop + base);
       int dec = PREC == 1 ? accept_fp64_warp(P, x, d->sw64, s, B.row_ptr + base, B.col, lane) : 2;
       if (dec == 2) {
         if (PREC == 1 && lane == 0) atomicAdd(&sg2[r], 1u);
@@ -671,6 +685,8 @@ cudaError_t batch_sweep(const BatchDev& B, const BatchLaunch& L, cudaStream_t st
   cudaError_t e;
   if ((e = cudaMemsetAsync(B.dcnt, 0, (size_t)B.pal_cap * sizeof(uint32_t), st)) != cudaSuccess)
     return e;
+  kb_propose<<<B.nblocks, kBatchBlock, 0, st>>>(B);
+  ++*L.launches;
   if (B.precision == 1)
     e = launch_coop(kb_sweep<1>, (unsigned)L.sweep_grid, 128, batch_sweep_smem(B.R), st, B);
   else

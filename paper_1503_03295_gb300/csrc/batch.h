@@ -94,6 +94,7 @@ struct BatchDev {
   uint32_t* perm;      // Ntot, global sites sorted by (colour, global index)
   uint32_t* off;       // pal_cap + 1 class offsets
   uint32_t* defer;     // Ntot
+  double4_32a* prop;   // Ntot proposals {S', u} of the current MC step
   uint32_t* dcnt;      // pal_cap
   uint32_t* bcnt;      // 32 x pal_cap KW bucket sizes per level
   unsigned long long ns_limit;  // bound of every device-side wait

@@ -96,6 +96,7 @@ void free_all(sco_batch* b) {
   cudaFree(B.perm);
   cudaFree(B.off);
   cudaFree(B.defer);
+  cudaFree(B.prop);
   cudaFree(B.dcnt);
   cudaFree(B.bcnt);
   cudaFree(b->L.scan_tmp);
@@ -401,6 +402,7 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   A(&B.colour, N * sizeof(uint32_t));
   A(&B.perm, N * sizeof(uint32_t));
   A(&B.defer, N * sizeof(uint32_t));
+  A(&B.prop, N * sizeof(double4_32a));
   if (e == cudaSuccess) e = cudaMallocHost(&b->hcnt, n * sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMallocHost(&b->hctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = alloc_palette(b, 256);

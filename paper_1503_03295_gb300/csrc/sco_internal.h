@@ -116,8 +116,8 @@ cudaError_t bucket_run(const DevParams& P, uint32_t g, ColourBufs& b, DevCounter
 cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,
                       const uint32_t* off, uint32_t g, uint64_t step, int precision,
-                      uint8_t* acc, uint32_t* defer, uint32_t* dcnt, DevCounters* cnt,
-                      cudaStream_t st, int64_t* launches);
+                      uint8_t* acc, uint32_t* defer, uint32_t* dcnt, double4_32a* prop,
+                      DevCounters* cnt, cudaStream_t st, int64_t* launches);
 
 int num_sms();
 

@@ -10,6 +10,18 @@ namespace sco {
 
 namespace {
 
+// Draws the proposal of every site for MC step `step` (see take_proposal).
+__global__ void __launch_bounds__(256) k_propose(const DevParams P, uint64_t step,
+                                                 double4_32a* __restrict__ prop) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= P.N) return;
+  SiteCtx c;
+  c.i = i;
+  const bool ok = propose(P, c, step);
+  prop[i] = ok ? make_double4_32a(c.Sn[0], c.Sn[1], c.Sn[2], c.u)
+               : make_double4_32a(0.0, 0.0, 1.0, -1.0);
+}
+
 // One thread per site of the class.  A site whose decision stays inside the error bound is
 // appended to the deferred list of the colour and settled by k_resolve (one warp per site),
 // so that no thread of this kernel runs the long FP64 / double-double evaluations.
@@ -21,7 +33,8 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) k_sweep(const DevParam
                                                const uint32_t* __restrict__ col,
                                                const uint32_t* __restrict__ perm,
                                                const uint32_t* __restrict__ off, uint32_t colour,
-                                               uint64_t step, uint8_t* __restrict__ acc,
+                                               const double4_32a* __restrict__ prop,
+                                               uint8_t* __restrict__ acc,
                                                uint32_t* __restrict__ defer,
                                                uint32_t* __restrict__ dcnt,
                                                DevCounters* __restrict__ cnt) {
@@ -31,7 +44,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) k_sweep(const DevParam
        idx += gridDim.x * blockDim.x) {
     SiteCtx c;
     load_site(P, c, perm[idx], s);
-    if (!propose(P, c, step)) {
+    if (!take_proposal(c, prop)) {
       acc[c.i] = 0;
       continue;
     }
@@ -62,7 +75,8 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
                                                  const uint32_t* __restrict__ off,
                                                  const uint32_t* __restrict__ defer,
                                                  const uint32_t* __restrict__ dcnt, uint32_t colour,
-                                                 uint64_t step, int fp32_screened,
+                                                 const double4_32a* __restrict__ prop,
+                                                 int fp32_screened,
                                                  uint8_t* __restrict__ acc,
                                                  DevCounters* __restrict__ cnt) {
   const uint32_t n = dcnt[colour], b = off[colour];
@@ -73,7 +87,7 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
   for (uint32_t q = warp; q < n; q += nwarps) {
     SiteCtx c;
     load_site(P, c, defer[b + q], s);
-    propose(P, c, step);  // the same proposal (a pure function of (seed, i, t))
+    take_proposal(c, prop);
     int d = fp32_screened ? accept_fp64_warp(P, c, sw, s, row_ptr, col, lane) : 2;
     if (d == 2) {
       ++ndd;
@@ -90,10 +104,12 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
 cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,
                       const uint32_t* off, uint32_t g, uint64_t step, int precision,
-                      uint8_t* acc, uint32_t* defer, uint32_t* dcnt, DevCounters* cnt,
-                      cudaStream_t st, int64_t* launches) {
+                      uint8_t* acc, uint32_t* defer, uint32_t* dcnt, double4_32a* prop,
+                      DevCounters* cnt, cudaStream_t st, int64_t* launches) {
   cudaError_t e = cudaMemsetAsync(dcnt, 0, (size_t)g * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
+  k_propose<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P, step, prop);
+  ++*launches;
   const unsigned nres = (unsigned)(2 * num_sms());
   // one launch per colour in ascending order; a class holds about N / g sites
   const int64_t per = P.N / (g > 0 ? g : 1) + 1;
@@ -104,11 +120,11 @@ cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float* s32,
   for (uint32_t c = 0; c < g; ++c) {
     if (precision == 1)
       k_sweep<1><<<(unsigned)nb, 128, 0, st>>>(P, t.sw64, t.sw32, s, s32, row_ptr, col, perm,
-                                                off, c, step, acc, defer, dcnt, cnt);
+                                                off, c, prop, acc, defer, dcnt, cnt);
     else
       k_sweep<0><<<(unsigned)nb, 128, 0, st>>>(P, t.sw64, t.sw32, s, s32, row_ptr, col, perm,
-                                                off, c, step, acc, defer, dcnt, cnt);
-    k_resolve<<<nres, 128, 0, st>>>(P, t.sw64, s, s32, row_ptr, col, off, defer, dcnt, c, step,
+                                                off, c, prop, acc, defer, dcnt, cnt);
+    k_resolve<<<nres, 128, 0, st>>>(P, t.sw64, s, s32, row_ptr, col, off, defer, dcnt, c, prop,
                                     precision == 1 ? 1 : 0, acc, cnt);
     *launches += 2;
   }

@@ -217,6 +217,18 @@ __device__ __forceinline__ bool propose(const DevParams& P, SiteCtx& c, uint64_t
   return false;
 }
 
+// Proposals are drawn for every site of a lattice by k_propose before the colour classes of a
+// step run (they depend only on (seed, site, step)), one double4 {S'x, S'y, S'z, u} per site;
+// u = -1 marks a site whose 64 attempts were all rejected (no move).
+__device__ __forceinline__ bool take_proposal(SiteCtx& c, const double4_32a* __restrict__ prop) {
+  const double4_32a q = prop[c.i];
+  c.Sn[0] = q.x;
+  c.Sn[1] = q.y;
+  c.Sn[2] = q.z;
+  c.u = q.w;
+  return q.w >= 0.0;
+}
+
 __device__ __forceinline__ void load_site(const DevParams& P, SiteCtx& c, uint32_t i,
                                           const double* __restrict__ s) {
   c.i = i;
