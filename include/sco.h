@@ -120,9 +120,10 @@ sco_status sco_get_sizes(sco_ctx* c, int64_t* n_sites, int64_t* n_entries, int32
 /* Host copies of the graph: row_ptr (N + 1), col (n_entries), colour (N); NULL skips. */
 sco_status sco_get_graph(sco_ctx* c, uint32_t* row_ptr, uint32_t* col, uint32_t* colour);
 
-/* Host copies of the colour classes: perm (N sites sorted by (colour, index); for palettes
- * above 12288 colours the order inside a class is unspecified) and off (palette + 1
- * offsets). */
+/* Host copies of the colour classes: perm (N sites grouped by colour: off[c] .. off[c+1] - 1
+ * hold class c; inside a class, for palettes up to 12288 colours, sites come by tiles of 2048
+ * consecutive sites and inside a tile by degree then index; above that the order inside a class
+ * is unspecified) and off (palette + 1 offsets). */
 sco_status sco_get_classes(sco_ctx* c, uint32_t* perm, uint32_t* off);
 
 /* Accept bit per site of the last MC step (N bytes, host). */

@@ -248,7 +248,9 @@ sco_status do_colour(sco_ctx* c) {
     c->cb.scan_tmp = nullptr;
     const uint32_t cap = c->g + 64;
     const int64_t ntiles = (c->P.N + kClassTileSites - 1) / kClassTileSites;
-    const int64_t tc = (int64_t)(cap < kMaxStablePalette ? cap : kMaxStablePalette) * ntiles + 1;
+    // (colour, degree bin) keys per tile: at most max(palette, 8192) (see bucket_run)
+    const int64_t keys = cap < kMaxStablePalette ? cap : kMaxStablePalette;
+    const int64_t tc = (keys > 8192 ? keys : 8192) * ntiles + 1;
     SCO_TRY(cudaMalloc(&c->cb.hist, (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.off, (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.cursor, (cap + 1) * sizeof(uint32_t)));
@@ -260,7 +262,7 @@ sco_status do_colour(sco_ctx* c) {
   }
   SCO_TRY(kw_run(c->P, c->row_ptr, c->col, c->g, c->p.colour_variant, c->cb, c->cnt, c->st,
                  &c->launches));
-  SCO_TRY(bucket_run(c->P, c->g, c->cb, c->cnt, c->st, &c->launches));
+  SCO_TRY(bucket_run(c->P, c->g, c->row_ptr, c->cb, c->cnt, c->st, &c->launches));
   c->colour_valid = true;
   return SCO_OK;
 }

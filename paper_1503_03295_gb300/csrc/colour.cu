@@ -171,48 +171,76 @@ __global__ void k_nonempty(uint32_t g, const uint32_t* __restrict__ hist,
   if ((threadIdx.x & 31) == 0 && n) atomicAdd(&cnt->n_colours, n);
 }
 
-// Stable colour classes: tiles of kClassTile sites count their colours, an exclusive scan
-// over (colour, tile) gives every tile its start inside every class, and one warp per tile
-// places the sites in ascending order.  perm is then sites sorted by (colour, index), the
-// order of the oracle, and consecutive threads of a sweep visit neighbouring sites.
+// Colour classes: tiles of kClassTile sites count their (colour, degree bin) keys, an
+// exclusive scan over (colour, tile, degree bin) gives every tile its start inside every class,
+// and one warp per tile places its sites.  Inside a class the sites come tile by tile (so
+// consecutive threads of a sweep visit nearby sites) and, inside a tile, by degree then index:
+// the 32 lanes of a sweep warp then loop over rows of nearly equal length.  The order inside a
+// class does not change any result (sites of one colour never interact).
 constexpr int kClassTile = (int)kClassTileSites;
 
-__global__ void k_tile_hist(uint32_t N, uint32_t g, uint32_t ntiles,
-                            const uint32_t* __restrict__ colour, uint32_t* __restrict__ tcnt) {
+// degree bins per colour: a power of two with g * bins <= 8192 (32 KB of counters), at most 64
+inline uint32_t deg_bins(uint32_t g) {
+  uint32_t d = 64;
+  while (d > 1 && (uint64_t)g * d > 8192) d >>= 1;
+  return d;
+}
+
+__device__ __forceinline__ uint32_t class_key(uint32_t v, const uint32_t* __restrict__ colour,
+                                              const uint32_t* __restrict__ row_ptr,
+                                              uint32_t dk) {
+  const uint32_t deg = row_ptr[v + 1] - row_ptr[v];
+  return colour[v] * dk + min(deg, dk - 1);
+}
+
+__global__ void k_tile_hist(uint32_t N, uint32_t g, uint32_t dk, uint32_t ntiles,
+                            const uint32_t* __restrict__ colour,
+                            const uint32_t* __restrict__ row_ptr, uint32_t* __restrict__ tcnt) {
   extern __shared__ uint32_t h[];
-  for (uint32_t c = threadIdx.x; c < g; c += blockDim.x) h[c] = 0;
+  const uint32_t nk = g * dk;
+  for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) h[k] = 0;
   __syncthreads();
   const uint32_t v0 = blockIdx.x * kClassTile;
   const uint32_t v1 = min(N, v0 + kClassTile);
-  for (uint32_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) atomicAdd(&h[colour[v]], 1u);
+  for (uint32_t v = v0 + threadIdx.x; v < v1; v += blockDim.x)
+    atomicAdd(&h[class_key(v, colour, row_ptr, dk)], 1u);
   __syncthreads();
-  for (uint32_t c = threadIdx.x; c < g; c += blockDim.x) tcnt[(size_t)c * ntiles + blockIdx.x] = h[c];
-  if (blockIdx.x == 0 && threadIdx.x == 0) tcnt[(size_t)g * ntiles] = 0;
+  for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
+    const uint32_t c = k / dk, d = k - c * dk;
+    tcnt[((size_t)c * ntiles + blockIdx.x) * dk + d] = h[k];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tcnt[(size_t)nk * ntiles] = 0;
 }
 
-__global__ void __launch_bounds__(32) k_tile_scatter(uint32_t N, uint32_t g, uint32_t ntiles,
+__global__ void __launch_bounds__(32) k_tile_scatter(uint32_t N, uint32_t g, uint32_t dk,
+                                                     uint32_t ntiles,
                                                      const uint32_t* __restrict__ colour,
+                                                     const uint32_t* __restrict__ row_ptr,
                                                      const uint32_t* __restrict__ base,
                                                      uint32_t* __restrict__ perm,
                                                      uint32_t* __restrict__ off) {
   extern __shared__ uint32_t run[];
   const int lane = threadIdx.x;
-  for (uint32_t c = lane; c < g; c += 32) run[c] = base[(size_t)c * ntiles + blockIdx.x];
+  const uint32_t nk = g * dk;
+  for (uint32_t k = lane; k < nk; k += 32) {
+    const uint32_t c = k / dk, d = k - c * dk;
+    run[k] = base[((size_t)c * ntiles + blockIdx.x) * dk + d];
+  }
   __syncwarp();
   const uint32_t v0 = blockIdx.x * kClassTile;
   const uint32_t v1 = min(N, v0 + kClassTile);
   for (uint32_t vb = v0; vb < v1; vb += 32) {
     const uint32_t v = vb + lane;
     const bool ok = v < v1;
-    const uint32_t c = ok ? colour[v] : 0xFFFFFFFFu;
-    const unsigned mask = __match_any_sync(0xffffffffu, c);
-    if (ok) perm[run[c] + __popc(mask & ((1u << lane) - 1u))] = v;
+    const uint32_t key = ok ? class_key(v, colour, row_ptr, dk) : 0xFFFFFFFFu;
+    const unsigned mask = __match_any_sync(0xffffffffu, key);
+    if (ok) perm[run[key] + __popc(mask & ((1u << lane) - 1u))] = v;
     __syncwarp();
-    if (ok && lane == __ffs(mask) - 1) run[c] += __popc(mask);
+    if (ok && lane == __ffs(mask) - 1) run[key] += __popc(mask);
     __syncwarp();
   }
   if (blockIdx.x == 0) {
-    for (uint32_t c = lane; c < g; c += 32) off[c] = base[(size_t)c * ntiles];
+    for (uint32_t c = lane; c < g; c += 32) off[c] = base[(size_t)c * ntiles * dk];
     if (lane == 0) off[g] = N;
   }
 }
@@ -338,21 +366,23 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   return cudaGetLastError();
 }
 
-cudaError_t bucket_run(const DevParams& P, uint32_t g, ColourBufs& b, DevCounters* cnt,
-                       cudaStream_t st, int64_t* launches) {
+cudaError_t bucket_run(const DevParams& P, uint32_t g, const uint32_t* row_ptr, ColourBufs& b,
+                       DevCounters* cnt, cudaStream_t st, int64_t* launches) {
   const int64_t N = P.N;
   const uint32_t ntiles = (uint32_t)((N + kClassTile - 1) / kClassTile);
   if (g <= kMaxStablePalette) {
     cudaError_t e = cudaMemsetAsync(&cnt->n_colours, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    const size_t sh = (size_t)g * sizeof(uint32_t);
-    k_tile_hist<<<ntiles, 256, sh, st>>>((uint32_t)N, g, ntiles, b.colour, b.tile_cnt);
+    const uint32_t dk = deg_bins(g);
+    const size_t sh = (size_t)g * dk * sizeof(uint32_t);
+    k_tile_hist<<<ntiles, 256, sh, st>>>((uint32_t)N, g, dk, ntiles, b.colour, row_ptr,
+                                         b.tile_cnt);
     ++*launches;
-    e = scan_excl_u32(b.tile_cnt, b.tile_cnt, (int64_t)g * ntiles + 1, b.scan_tmp, nullptr, st,
-                      launches);
+    e = scan_excl_u32(b.tile_cnt, b.tile_cnt, (int64_t)g * dk * ntiles + 1, b.scan_tmp, nullptr,
+                      st, launches);
     if (e != cudaSuccess) return e;
-    k_tile_scatter<<<ntiles, 32, sh, st>>>((uint32_t)N, g, ntiles, b.colour, b.tile_cnt, b.perm,
-                                          b.off);
+    k_tile_scatter<<<ntiles, 32, sh, st>>>((uint32_t)N, g, dk, ntiles, b.colour, row_ptr,
+                                          b.tile_cnt, b.perm, b.off);
     ++*launches;
     k_nonempty_off<<<1, 1024, 0, st>>>(g, b.off, cnt);
     ++*launches;

@@ -99,7 +99,7 @@ struct ColourBufs {
   uint32_t* cursor;  // g
   uint32_t* dcnt;    // g deferred sweep decisions per colour
   uint32_t* perm;    // N
-  uint32_t* tile_cnt;  // palette x tiles (+1) per-tile colour counts, scanned in place
+  uint32_t* tile_cnt;  // (colour, tile, degree bin) counts (+1), scanned in place
   uint64_t* scan_tmp;
   uint32_t* bcnt;    // 32 x palette KW bucket sizes per level
   uint32_t* meta;    // 6 words: one-lattice view of the persistent colouring kernel
@@ -109,8 +109,8 @@ constexpr int64_t kClassTileSites = 2048;
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
                    uint32_t g, int variant, ColourBufs& b, DevCounters* cnt, cudaStream_t st,
                    int64_t* launches);
-cudaError_t bucket_run(const DevParams& P, uint32_t g, ColourBufs& b, DevCounters* cnt,
-                       cudaStream_t st, int64_t* launches);
+cudaError_t bucket_run(const DevParams& P, uint32_t g, const uint32_t* row_ptr, ColourBufs& b,
+                       DevCounters* cnt, cudaStream_t st, int64_t* launches);
 
 // ---- sweep.cu ----
 cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float* s32,
