@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) kb_switch(const BatchDev B) {
                       &B.ctl->ovf_n, &B.ctl->ovf_full, gs};
     const size_t so = 3 * (size_t)base;
     const uint32_t n_out =
-        switch_site<PREC>(sP, T, Wtot, d->xy, d->xyq, d->xy32, B.s + so, B.s32 + so, epoch,
+        switch_site<PREC>(sP, T, Wtot, d->sw64, d->xyq, d->xy32, B.s + so, B.s32 + so, epoch,
                           d->mnn0, d->mnn1, i, o, n_dip, ghits, g32);
     B.hcnt[gs] = n_out;
     n_half = n_out;

@@ -82,10 +82,16 @@ __device__ __forceinline__ W4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint
   return o;
 }
 
-__device__ __forceinline__ double u53(uint64_t w) { return (double)(w >> 11) * 0x1p-53; }
-__device__ __forceinline__ double u53pos(uint64_t w) {
-  return ((double)(w >> 11) + 1.0) * 0x1p-53;
+// m 2^-53 for an integer 0 <= m <= 2^53, built from its bits (integer operations only, exact;
+// 64-bit integer conversions would run on the FP64 pipe).
+__device__ __forceinline__ double scaled53(uint64_t m) {
+  if (m == 0) return 0.0;
+  const int e = 63 - __clzll((long long)m);  // m in [2^e, 2^(e+1)), e <= 53
+  const uint64_t mant = e <= 52 ? (m << (52 - e)) & 0xFFFFFFFFFFFFFull : 0ull;
+  return __longlong_as_double((long long)(((uint64_t)(e - 53 + 1023) << 52) | mant));
 }
+__device__ __forceinline__ double u53(uint64_t w) { return scaled53(w >> 11); }
+__device__ __forceinline__ double u53pos(uint64_t w) { return scaled53((w >> 11) + 1); }
 
 // Marsaglia (1972): reject unless 0 < s = a1^2 + a2^2 < 1, then
 // S = (2 a1 sqrt(1-s), 2 a2 sqrt(1-s), 1 - 2s).  Each operation rounded on its own so that
@@ -158,7 +164,7 @@ struct __align__(64) Sw64 {
   double ax, ay;    // |dx|, |dy|
   double bvm;       // fl(beta Vmax)
   double c0;        // bound on |error of x| not scaling with |x|, plus 2^-52 (2 beta Vmax)
-  double pad;
+  double bsw;       // margin bound of the FP64 survival test of the switch (see table.cu)
 };
 
 // x with its sign flipped when neg (bit operation, no FP64 instruction)

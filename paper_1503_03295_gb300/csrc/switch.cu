@@ -12,7 +12,7 @@ namespace {
 template <int PREC>
 __global__ void __launch_bounds__(256) k_switch(const DevParams P, const uint64_t* __restrict__ W,
                                                 const uint32_t* __restrict__ disp,
-                                                const double2* __restrict__ xy,
+                                                const Sw64* __restrict__ sw64,
                                                 const double* __restrict__ xyq,
                                                 const float4* __restrict__ xy32,
                                                 const double* __restrict__ s,
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) k_switch(const DevParams P, const uint64_
     const uint64_t Wtot = P.K > 0 ? __ldg(&W[P.K - 1]) : 0;
     const SwitchOut o{b.hslot + i * (int64_t)kSlotCap, b.indeg, b.ovf, b.ovf_cap, &cnt->ovf_n,
                       &cnt->ovf_full, (uint32_t)i};
-    const uint32_t n_out = switch_site<PREC>(P, T, Wtot, xy, xyq, xy32, s, s32, epoch, mnn0,
+    const uint32_t n_out = switch_site<PREC>(P, T, Wtot, sw64, xyq, xy32, s, s32, epoch, mnn0,
                                              mnn1, (uint32_t)i, o, n_dip, ghits, g32);
     b.hcnt[i] = n_out;
     n_half = n_out;
@@ -116,10 +116,10 @@ cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, cons
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((P.N + 255) / 256);
   if (precision == 1)
-    k_switch<1><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.xy, t.xyq, t.xy32, s, s32, epoch,
+    k_switch<1><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.sw64, t.xyq, t.xy32, s, s32, epoch,
                                      t.m_nn[0], t.m_nn[1], b, cnt);
   else
-    k_switch<0><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.xy, t.xyq, t.xy32, s, s32, epoch,
+    k_switch<0><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.sw64, t.xyq, t.xy32, s, s32, epoch,
                                      t.m_nn[0], t.m_nn[1], b, cnt);
   ++*launches;
   return cudaGetLastError();

@@ -73,26 +73,21 @@ __device__ __noinline__ int64_t next_candidate_dd(const DevParams& P, const Near
 
 __device__ __forceinline__ int64_t next_candidate(const DevParams& P, const NearTable& T,
                                                   int64_t s, uint64_t Ws, uint64_t Wtot,
-                                                  uint64_t wE, unsigned& ghits) {
-  if (s >= T.K - 1 || !P.switching) return T.K;
-  const double up = u53pos(wE);
-  const double tau = -log(up) * P.inv_bD58;
-  const uint64_t rem = Wtot - Ws;
-  int64_t k = T.K;
-  if (tau <= (double)rem) k = T.lower_bound(s + 1, Ws + __double2ull_ru(tau));
-  // tau carries < 2^-49 relative error (log, fl(beta D), fl(2^58 / bD), one product): guard
-  // at 2^-46
-  const double eps = 0x1p-46;
-  bool certain = true;
-  if (k < T.K && !((double)(T.w(k) - Ws) >= tau * (1.0 + eps))) certain = false;
-  if (k - 1 > s && !((double)(T.w(k - 1) - Ws) < tau * (1.0 - eps))) certain = false;
-  if (certain) return k;
-  ++ghits;
-  return next_candidate_dd(P, T, s, Ws, up);
-}
+                                                  uint64_t wE, unsigned& ghits);
 
 // ceil(x) as an integer for finite x >= 0 (saturating at 2^64 - 1), from the bits of x with
 // integer operations only (64-bit conversions would run on the FP64 pipe).
+__device__ __forceinline__ uint64_t ceil_u64d(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  if (b == 0ull || (b >> 63)) return 0ull;
+  const int ex = (int)((b >> 52) & 0x7FFu) - 1075;  // x = mant * 2^ex
+  const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  if (ex >= 0) return ex >= 11 ? ~0ull : mant << ex;
+  if (ex <= -54) return 1ull;  // 0 < x < 1
+  const uint64_t q = mant >> (-ex);
+  return q + ((q << (-ex)) != mant ? 1ull : 0ull);
+}
+
 __device__ __forceinline__ uint64_t ceil_u64(float x) {
   const uint32_t b = __float_as_uint(x);
   if (b == 0u || (b >> 31)) return 0ull;
@@ -102,6 +97,30 @@ __device__ __forceinline__ uint64_t ceil_u64(float x) {
   if (ex <= -25) return 1ull;  // 0 < x < 1
   const uint64_t q = mant >> (-ex);
   return q + ((q << (-ex)) != mant ? 1ull : 0ull);
+}
+
+// tau = -ln(u+) / (beta D 2^-58) carries < 2^-49 relative error (log, fl(beta D), fl(2^58 / bD),
+// one product); the candidate is certain when W_k - W_s >= tau (1 + 2^-46) and
+// W_(k-1) - W_s < tau (1 - 2^-46), compared as integers (ceil of the bounds).
+__device__ __forceinline__ int64_t next_candidate(const DevParams& P, const NearTable& T,
+                                                  int64_t s, uint64_t Ws, uint64_t Wtot,
+                                                  uint64_t wE, unsigned& ghits) {
+  if (s >= T.K - 1 || !P.switching) return T.K;
+  const double up = u53pos(wE);
+  const double tau = -log(up) * P.inv_bD58;
+  const uint64_t rem = Wtot - Ws;
+  const uint64_t thr = ceil_u64d(tau);
+  int64_t k = T.K;
+  if (thr <= rem) k = T.lower_bound(s + 1, Ws + thr);
+  const double eps = 0x1p-46;
+  const uint64_t hi = ceil_u64d(tau * (1.0 + eps));  // W_k - W_s >= hi: surely a candidate
+  const uint64_t lo = ceil_u64d(tau * (1.0 - eps));  // W_k-1 - W_s < lo: surely not
+  bool certain = true;
+  if (k < T.K && T.w(k) - Ws < hi) certain = false;
+  if (k - 1 > s && T.w(k - 1) - Ws >= lo) certain = false;
+  if (certain) return k;
+  ++ghits;
+  return next_candidate_dd(P, T, s, Ws, up);
 }
 
 // FP32 screen of the candidate search.  E = -ln u+ is taken as -log1pf(-(1 - u+)) above 1/2
@@ -157,24 +176,23 @@ __device__ __noinline__ bool survives_dd(const DevParams& P, const double* Si, c
   return dd_lt(dd_mul_d(q, u1), pr);
 }
 
-// FP64 survival test with its error bound: |dV| <= 2^-47 Dc r^2, fl(Vmax) within 2^-52,
-// the library's expm1_np within kExpm1RelErr (1 - P), the table's q (CUDA expm1) within 4 ulp, so
-// 1 - P and q within the terms below (doubled for margin).
-__device__ __forceinline__ bool survives_fp64(const DevParams& P, double Dc, double Vm, double q,
-                                              double r2, const double* Si, const double* Sj,
-                                              int32_t dx, int32_t dy, uint64_t A, double u1,
+// FP64 survival test u q < 1 - P_ij: x = beta (V - Vmax) from the beta-scaled pair table
+// (t, the sweep's Sw64 entry), 1 - P = -expm1_np(x), margin bound t.bsw (precomputed: |dx| <=
+// c0, expm1_np within kExpm1RelErr, q within 2^-50, two roundings; doubled).  u is exact.
+__device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t, double q,
+                                              const double* Si, const double* Sj, int32_t dx,
+                                              int32_t dy, uint64_t A, double u1,
                                               unsigned& ghits) {
-  const double V = pair_V(Dc, r2, Si[0], Si[1], Si[2], Sj[0], Sj[1], Sj[2], (double)dx,
-                          (double)dy);
-  const double b = P.beta * (V - Vm);
-  const double pr = -expm1_np(b);  // q = -expm1(-fl(2 beta Vmax)) comes from the table
+  const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
+  const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
+  const double ss = Si[0] * Sj[0] + Si[1] * Sj[1] + Si[2] * Sj[2];
+  const double pa = Si[0] * ax3 + Si[1] * ay3;
+  const double pb = Sj[0] * fx + Sj[1] * fy;
+  const double b = (t.a1 * ss - pa * pb) - t.bvm;
+  const double pr = -expm1_np(b);
   const double mu = pr - u1 * q;
-  const double dV = 0x1p-47 * Dc * r2;
-  const double B =
-      2.0 * (P.beta * (dV + 0x1p-52 * Vm) + 0x1p-52 * fabs(b) + 2.0 * kExpm1RelErr * fabs(pr) +
-             0x1p-49 * q);
-  if (mu > B) return true;
-  if (mu < -B) return false;
+  if (mu > t.bsw) return true;
+  if (mu < -t.bsw) return false;
   ++ghits;
   return survives_dd(P, Si, Sj, dx, dy, A, u1);
 }
@@ -182,8 +200,9 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, double Dc, dou
 // FP32 screen of the same test (FP32-guarded form): spins from the FP32 shadow
 // (|dS| <= 2^-24 per component), table constants rounded to FP32, expm1f within 4 ulp.
 // Falls through to the FP64 test (and from there to double-double) inside the bound.
-__device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32, double Dc,
-                                              double Vm, double q64, const float* Si32,
+__device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
+                                              const Sw64* __restrict__ sw, double q64,
+                                              const float* Si32,
                                               const float* Sj32, const double* Si,
                                               const double* Sj, int32_t dx, int32_t dy,
                                               uint64_t A, uint64_t wU, unsigned& g32,
@@ -208,8 +227,8 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32, do
   if (mu > B) return true;
   if (mu < -B) return false;
   ++g32;
-  return survives_fp64(P, Dc, Vm, q64, (double)dx * dx + (double)dy * dy, Si, Sj, dx, dy, A,
-                       u53(wU), ghits);
+  const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy);
+  return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, A, u53(wU), ghits);
 }
 
 // Where site i writes its upper neighbours: kSlotCap slots of its own, then an overflow list
@@ -228,7 +247,7 @@ struct SwitchOut {
 // upper neighbours written (dipolar survivors plus exchange-only bonds).
 template <int PREC>
 __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTable& T,
-                                                uint64_t Wtot, const double2* __restrict__ xy,
+                                                uint64_t Wtot, const Sw64* __restrict__ sw,
                                                 const double* __restrict__ xyq,
                                                 const float4* __restrict__ xy32,
                                                 const double* __restrict__ s,
@@ -280,16 +299,14 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
       const int64_t j = xj + (int64_t)P.Lx * yj;
       const uint64_t A = Wk - (k > 0 ? T.w(k - 1) : 0ull);
       const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
-      const double2 t = __ldg(&xy[tix]);
       const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
       bool surv;
       if (PREC == 1) {
         const float Sj32[3] = {s32[j], s32[P.N + j], s32[2 * P.N + j]};
-        surv = survives_fp32(P, __ldg(&xy32[tix]), t.x, t.y, __ldg(&xyq[tix]), Si32, Sj32, Si,
-                             Sj, dx, dy, A, wU, g32, ghits);
+        surv = survives_fp32(P, __ldg(&xy32[tix]), sw, __ldg(&xyq[tix]), Si32, Sj32, Si, Sj, dx,
+                             dy, A, wU, g32, ghits);
       } else {
-        surv = survives_fp64(P, t.x, t.y, __ldg(&xyq[tix]), (double)dx * dx + (double)dy * dy,
-                             Si, Sj, dx, dy, A, u53(wU), ghits);
+        surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), Si, Sj, dx, dy, A, u53(wU), ghits);
       }
       if (surv) {
         emit((uint32_t)j);

@@ -72,7 +72,7 @@ __global__ void k_hazard(int64_t K, const uint32_t* __restrict__ disp, uint64_t*
 // so x = beta V - fl(beta Vmax) = S_i . f - bvm; c0 bounds the part of |x error| that does not
 // scale with |x|: |beta dV| <= 2^-46 beta Dc r^2 (FP64 products, the rounded beta-scaled
 // constants) plus 2^-51 beta Vmax (fl(beta Vmax)), plus 2^-52 (2 beta Vmax) for the rounding of
-// x itself (|x| <= 2 beta Vmax).  FP32 (float4 {A1, A3, beta Vmax, c0}): V(S) = S.f with
+// x itself (|x| <= 2 beta Vmax).  The switch's survival test uses the same x.  FP32 (float4 {A1, A3, beta Vmax, c0}): V(S) = S.f with
 // f = A1 S_j - A3 (S_j.d) d, |dV| <= 2^-16 Dc r^2 (shadow spins, FP32 constants).
 __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __restrict__ xy,
                      double* __restrict__ xyq, float4* __restrict__ xy32,
@@ -102,7 +102,10 @@ __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __r
   t.ay = (double)ay;
   t.bvm = bvm;
   t.c0 = c64 * (1.0 + 0x1p-20);
-  t.pad = 0.0;
+  // survival test of the switch: mu = (1 - P) - u q with 1 - P = -expm1_np(x): |d(1 - P)| <=
+  // |dx| + eps_z <= c0 + kExpm1RelErr; q (CUDA expm1 of a rounded 2 beta Vmax) within 2^-50;
+  // the product u q and the difference 2^-52 each.  Doubled.
+  t.bsw = 2.0 * (c64 + kExpm1RelErr + 0x1p-49) * (1.0 + 0x1p-20);
   sw64[q] = t;
   const double c32 = beta * (0x1p-16 * dc * (double)r2) + 0x1p-21 * bvm;
   sw32[q] = make_float4((float)a1, (float)a3, (float)bvm, (float)(c32 * (1.0 + 0x1p-20)));
