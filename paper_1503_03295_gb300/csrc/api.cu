@@ -303,6 +303,9 @@ void free_all(sco_ctx* c) {
   cudaFree(c->cb.scan_tmp);
   cudaFree(c->cb.bcnt);
   cudaFree(c->cb.meta);
+  cudaFree(c->cb.imask);
+  cudaFree(c->cb.imeta);
+  cudaFree(c->cb.ilist);
   cudaFree(c->acc);
   cudaFree(c->defer);
   cudaFree(c->prop);
@@ -371,6 +374,9 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.colour, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.perm, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.meta, 8 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cb.imask, N * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cb.imeta, N * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cb.ilist, 8 * N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->acc, N);
   if (e == cudaSuccess) e = cudaMalloc(&c->defer, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->prop, N * sizeof(double4_32a));

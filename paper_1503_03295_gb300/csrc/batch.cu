@@ -657,6 +657,10 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
     V.pal = B.pal_cap;
     V.levels = L.levels;
     V.ns_limit = B.ns_limit;
+    V.imask = B.imask;
+    V.imeta = B.imeta;
+    V.ilist = B.ilist;
+    V.gmax = &B.ctl->gmax;
     if ((e = launch_coop(k_kw_bcr, (unsigned)L.kw_grid, 256, kw_bcr_smem(B.R, B.pal_cap), st,
                          V)) != cudaSuccess)
       return e;

@@ -97,6 +97,9 @@ struct BatchDev {
   double4_32a* prop;   // Ntot proposals {S', u} of the current MC step
   uint32_t* dcnt;      // pal_cap
   uint32_t* bcnt;      // 32 x pal_cap KW bucket sizes per level
+  unsigned long long* imask;  // Ntot per-level vertex records of the colouring kernel
+  uint32_t* imeta;            // Ntot
+  uint32_t* ilist;            // 8 Ntot (kItemList per record)
   unsigned long long ns_limit;  // bound of every device-side wait
 };
 

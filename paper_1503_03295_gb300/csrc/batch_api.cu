@@ -97,6 +97,9 @@ void free_all(sco_batch* b) {
   cudaFree(B.off);
   cudaFree(B.defer);
   cudaFree(B.prop);
+  cudaFree(B.imask);
+  cudaFree(B.imeta);
+  cudaFree(B.ilist);
   cudaFree(B.dcnt);
   cudaFree(B.bcnt);
   cudaFree(b->L.scan_tmp);
@@ -403,6 +406,9 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   A(&B.perm, N * sizeof(uint32_t));
   A(&B.defer, N * sizeof(uint32_t));
   A(&B.prop, N * sizeof(double4_32a));
+  A(&B.imask, N * sizeof(unsigned long long));
+  A(&B.imeta, N * sizeof(uint32_t));
+  A(&B.ilist, 8 * N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMallocHost(&b->hcnt, n * sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMallocHost(&b->hctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = alloc_palette(b, 256);

@@ -331,6 +331,10 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     V.pal = g;
     V.levels = M;
     V.ns_limit = ns_limit;
+    V.imask = b.imask;
+    V.imeta = b.imeta;
+    V.ilist = b.ilist;
+    V.gmax = nullptr;
     void* args[] = {(void*)&V};
     e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr, dim3((unsigned)(bps * num_sms())),
                                     dim3(256), args, sh, st);

@@ -39,7 +39,126 @@ struct KwView {
   unsigned pal;                 // >= every g, <= kBcrMaxPalette
   unsigned levels;              // >= every M, <= kBcrMaxLevels - 1
   unsigned long long ns_limit;  // bound of every barrier wait
+  // Per-level records of the bucketed vertices (optional: null keeps the row path).  Item q
+  // of the current level: the colours of its left-half same-group neighbours (imask, final
+  // at this level), and its same-group right-half neighbours of larger previous colour
+  // (ilist[kItemList q ..], global indices; imeta = their count, or kItemSlow above that).
+  unsigned long long* imask;
+  uint32_t* imeta;
+  uint32_t* ilist;
+  const unsigned* gmax;         // optional: largest palette on the device (else pal)
 };
+
+constexpr int kItemList = 8;
+constexpr uint32_t kItemSlow = 0x100;
+
+__device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t* p) {
+  uint4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+
+// Builds the record of item pos (vertex gv, previous colour c) at level p, while every colour
+// still holds its value from level p - 1: left-half same-group neighbours go into the mask
+// (their colours are final at this level), right-half ones of larger previous colour into the
+// list; smaller ones are ignored (they keep colours >= g while gv's bucket runs).  Palettes
+// of at most 64 colours.
+__device__ __forceinline__ void kw_item_build(const KwView& V, uint32_t pos, uint32_t gv,
+                                              uint32_t base, uint32_t c, unsigned p,
+                                              unsigned long long M) {
+  const uint32_t v = gv - base;
+  const uint32_t grp = fdiv(v, M) >> p;
+  const uint32_t b = V.row_ptr[gv], e = V.row_ptr[gv + 1];
+  const unsigned long long* word = V.word + base;
+  unsigned long long mask = 0;
+  uint32_t n = 0;
+  uint32_t* out = V.ilist + (size_t)pos * kItemList;
+  for (uint32_t q0 = b; q0 < e; q0 += 16) {
+    uint32_t uu[16];
+    unsigned long long ww[16];
+#pragma unroll
+    for (int a = 0; a < 16; ++a) uu[a] = q0 + a < e ? (V.col[q0 + a] & kIndexMask) : kNone;
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+      ww[a] = 0;
+      if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) ww[a] = ld_relaxed(&word[uu[a]]);
+      else uu[a] = kNone;
+    }
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+      if (uu[a] == kNone) continue;
+      const uint32_t cu = (uint32_t)(ww[a] & kColMask);
+      if (!((fdiv(uu[a], M) >> (p - 1)) & 1u)) {
+        mask |= 1ull << (cu & 63);
+      } else if (cu > c) {
+        if (n < (uint32_t)kItemList) out[n] = base + uu[a];
+        ++n;
+      }
+    }
+  }
+  V.imask[pos] = mask;
+  V.imeta[pos] = n > (uint32_t)kItemList ? kItemSlow : n;
+}
+
+// An item's record, loaded ahead of its bucket.
+struct KwItem {
+  uint32_t gv;    // global vertex (kNone: no item)
+  uint32_t meta;  // listed neighbours, or kItemSlow
+  unsigned long long mask;
+  uint32_t u[kItemList];
+};
+
+__device__ __forceinline__ void kw_item_fetch(KwItem& it, const KwView& V, uint32_t pos) {
+  it.gv = ld_u32_gpu(&V.list[pos]);
+  it.meta = ld_u32_gpu(&V.imeta[pos]);
+  it.mask = ld_relaxed(&V.imask[pos]);
+  const uint32_t* src = V.ilist + (size_t)pos * kItemList;
+#pragma unroll
+  for (int a = 0; a < kItemList; a += 4) {
+    const uint4 x = ld_relaxed_v4(src + a);
+    it.u[a] = x.x;
+    it.u[a + 1] = x.y;
+    it.u[a + 2] = x.z;
+    it.u[a + 3] = x.w;
+  }
+}
+
+// Recolours an item from its record: the listed neighbours are final (bounded wait otherwise,
+// which the bucket order rules out); new colour = smallest one free of mask and their
+// colours, round = 1 + their largest round.
+__device__ __forceinline__ bool kw_item_recolour(const KwItem& it, const KwView& V, unsigned p,
+                                                 unsigned& rmax, unsigned long long t_start) {
+  const uint32_t n = it.meta;
+  unsigned long long ww[kItemList];
+#pragma unroll
+  for (int a = 0; a < kItemList; ++a) ww[a] = (uint32_t)a < n ? ld_relaxed(&V.word[it.u[a]]) : 0;
+  unsigned long long mask = it.mask;
+  unsigned rv = 0;
+#pragma unroll
+  for (int a = 0; a < kItemList; ++a) {
+    if ((uint32_t)a >= n) continue;
+    unsigned long long wu = ww[a];
+    unsigned spins = 0;
+    while (tag_of(wu) != p) {
+      __nanosleep(64);
+      wu = ld_relaxed(&V.word[it.u[a]]);
+      if ((++spins & 255) == 0 &&
+          (global_ns() - t_start > V.ns_limit || ld_status(V.status) != 0)) {
+        atomicCAS(V.status, 0, kStatusTimeout);
+        return false;
+      }
+    }
+    mask |= 1ull << ((uint32_t)(wu & kColMask) & 63);
+    rv = max(rv, rnd_of(wu));
+  }
+  const unsigned cn = (unsigned)(__ffsll((long long)~mask) - 1);
+  rmax = max(rmax, rv + 1);
+  st_relaxed(&V.word[it.gv], pack(p, rv + 1, cn));
+  return true;
+}
 
 // The row of a vertex with its first sixteen neighbour entries, loaded ahead of its turn.
 struct KwRow {
@@ -152,6 +271,8 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
   for (int r = threadIdx.x; r <= R; r += blockDim.x) sbase[r] = V.site_start[r];
   const uint32_t nth = gridDim.x * blockDim.x;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  // records (instead of rows) when every palette fits a 64-bit mask
+  const bool fast = V.imask != nullptr && (V.gmax ? *V.gmax : pal) <= 64u;
   bool ok = true;
   for (unsigned p = 1; p <= V.levels && ok; ++p) {
     // right-half slots of every lattice at level p
@@ -201,7 +322,12 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
       const uint32_t gv = vertex_of(slot);
       if (gv == kNone) continue;
       const uint32_t c = (uint32_t)(ld_relaxed(&V.word[gv]) & kColMask);
-      V.list[start[c] + offb[c] + atomicAdd(&lcur[c], 1u)] = gv;
+      const uint32_t pos = start[c] + offb[c] + atomicAdd(&lcur[c], 1u);
+      V.list[pos] = gv;
+      if (fast) {
+        const int r = find_le(sbase, R, gv);
+        kw_item_build(V, pos, gv, sbase[r], c, p, V.plan[r].magic);
+      }
     }
     if (!grid_sync(V.bar, V.status, V.ns_limit)) {
       ok = false;
@@ -217,31 +343,62 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
       return -1;
     };
     int c = next_bucket((int)pal);
-    KwRow w;
-    w.gv = kNone;
-    if (c >= 0 && gtid < start[c + 1] - start[c])
-      kw_fetch(w, ld_u32_gpu(&V.list[start[c] + gtid]), V.row_ptr, V.col);
-    while (c >= 0 && ok) {
-      const uint32_t b0 = start[c], n = start[c + 1] - b0;
-      bool mine = true;
-      for (uint32_t q = gtid; q < n && mine; q += nth) {
-        if (q != gtid) kw_fetch(w, ld_u32_gpu(&V.list[b0 + q]), V.row_ptr, V.col);
-        const uint32_t gv = w.gv;
-        const int r = find_le(sbase, R, gv);
-        const uint32_t base = sbase[r];
-        unsigned rm = 0;
-        mine = kw_recolour(gv - base, (uint32_t)c, w, p, V.plan[r].magic, V.col, V.word + base,
-                           rm, V.status, t_start, V.ns_limit);
-        atomicMax(&smax[r], rm);
+    if (fast) {
+      KwItem it;
+      it.gv = kNone;
+      if (c >= 0 && gtid < start[c + 1] - start[c]) kw_item_fetch(it, V, start[c] + gtid);
+      while (c >= 0 && ok) {
+        const uint32_t b0 = start[c], n = start[c + 1] - b0;
+        bool mine = true;
+        for (uint32_t q = gtid; q < n && mine; q += nth) {
+          if (q != gtid) kw_item_fetch(it, V, b0 + q);
+          const int r = find_le(sbase, R, it.gv);
+          unsigned rm = 0;
+          if (it.meta & kItemSlow) {  // more larger neighbours than the record holds
+            const uint32_t base = sbase[r];
+            KwRow w;
+            kw_fetch(w, it.gv, V.row_ptr, V.col);
+            mine = kw_recolour(it.gv - base, (uint32_t)c, w, p, V.plan[r].magic, V.col,
+                               V.word + base, rm, V.status, t_start, V.ns_limit);
+          } else {
+            mine = kw_item_recolour(it, V, p, rm, t_start);
+          }
+          atomicMax(&smax[r], rm);
+        }
+        grid_arrive(V.bar, s_old);
+        const int cn = next_bucket(c);
+        it.gv = kNone;
+        if (cn >= 0 && gtid < start[cn + 1] - start[cn]) kw_item_fetch(it, V, start[cn] + gtid);
+        ok = grid_wait(V.bar, s_old, V.status, V.ns_limit);
+        c = cn;
       }
-      grid_arrive(V.bar, s_old);
-      const int cn = next_bucket(c);
+    } else {
+      KwRow w;
       w.gv = kNone;
-      if (cn >= 0 && gtid < start[cn + 1] - start[cn])
-        kw_fetch(w, ld_u32_gpu(&V.list[start[cn] + gtid]), V.row_ptr, V.col);
-      // false for every block once an error was reported (status read after the barrier)
-      ok = grid_wait(V.bar, s_old, V.status, V.ns_limit);
-      c = cn;
+      if (c >= 0 && gtid < start[c + 1] - start[c])
+        kw_fetch(w, ld_u32_gpu(&V.list[start[c] + gtid]), V.row_ptr, V.col);
+      while (c >= 0 && ok) {
+        const uint32_t b0 = start[c], n = start[c + 1] - b0;
+        bool mine = true;
+        for (uint32_t q = gtid; q < n && mine; q += nth) {
+          if (q != gtid) kw_fetch(w, ld_u32_gpu(&V.list[b0 + q]), V.row_ptr, V.col);
+          const uint32_t gv = w.gv;
+          const int r = find_le(sbase, R, gv);
+          const uint32_t base = sbase[r];
+          unsigned rm = 0;
+          mine = kw_recolour(gv - base, (uint32_t)c, w, p, V.plan[r].magic, V.col, V.word + base,
+                             rm, V.status, t_start, V.ns_limit);
+          atomicMax(&smax[r], rm);
+        }
+        grid_arrive(V.bar, s_old);
+        const int cn = next_bucket(c);
+        w.gv = kNone;
+        if (cn >= 0 && gtid < start[cn + 1] - start[cn])
+          kw_fetch(w, ld_u32_gpu(&V.list[start[cn] + gtid]), V.row_ptr, V.col);
+        // false for every block once an error was reported (status read after the barrier)
+        ok = grid_wait(V.bar, s_old, V.status, V.ns_limit);
+        c = cn;
+      }
     }
     __syncthreads();
     for (int r = threadIdx.x; r < R; r += blockDim.x)

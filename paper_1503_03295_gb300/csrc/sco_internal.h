@@ -103,6 +103,9 @@ struct ColourBufs {
   uint64_t* scan_tmp;
   uint32_t* bcnt;    // 32 x palette KW bucket sizes per level
   uint32_t* meta;    // 6 words: one-lattice view of the persistent colouring kernel
+  unsigned long long* imask;  // N per-level vertex records of the colouring kernel
+  uint32_t* imeta;            // N
+  uint32_t* ilist;            // 8 N (kItemList per record)
 };
 constexpr uint32_t kMaxStablePalette = 12288;  // palettes up to this size get stable classes
 constexpr int64_t kClassTileSites = 2048;
