@@ -180,6 +180,11 @@ __device__ __forceinline__ bool neg_strict(double x) {
 __device__ __forceinline__ unsigned long long pos_bits(double x) {
   return (unsigned long long)__double_as_longlong(x);
 }
+// biased exponent field of a double >= 0 (x >= 2^(e - 1023) for normal x; 0 for zero and
+// subnormals, which then read as tiny)
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF;
+}
 
 // ---------------------------------------------------------------------------------------
 // Double-double arithmetic (Dekker 1971; Knuth's two-sum; Hida, Li and Bailey's QD layout)

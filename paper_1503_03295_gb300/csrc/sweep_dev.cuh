@@ -42,8 +42,10 @@ constexpr int kScale32 = 60;
 //   z = -expm1(x) has relative error eps_z + |dx| / z;  log of a product of n factors adds
 //   n eps_r;  the logarithms eps_f |log P|;  sum (x_new - x_old) adds 2 sum c0 (the x errors)
 //   and (n + 2) eps_r sum |x_new - x_old| <= (n + 2) eps_r 2 sum bvm <= (n + 2) sum c0 (c0 >=
-//   2^-51 bvm by construction).  With zmin = min z, sum_j |dx_j| / z_j <= sum c0 / zmin, which
-//   must stay below 2^-10 (first order) or the decision is left undecided.
+//   2^-51 bvm by construction).  The first-order analysis needs lin = sum_j |dx_j| / z_j small:
+//   each ratio is below 2^(e(c0_j) - e(z_j) + 1) with e the exponent field, so with two z per
+//   pair lin <= n 2^(dmax + 2), dmax the largest exponent difference, found with integer
+//   operations; it must stay below 2^-10 or the decision is left undecided.
 
 // FP64 decision (0: reject, 1: accept, 2: undecided).  eps_r = 2^-52 (unit roundoff, with
 // margin), eps_f = 2^-50 for the CUDA logarithms (within 4 ulp), eps_z = kExpm1RelErr for the
@@ -57,7 +59,7 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
   const double S0 = c.S[0], S1 = c.S[1], S2 = c.S[2];
   const double N0 = c.Sn[0], N1 = c.Sn[1], N2 = c.Sn[2];
   double bdv = 0.0, pz_o = 1.0, pz_n = 1.0, c0s = 0.0;
-  unsigned long long zmin_b = pos_bits(1.0);
+  int dmax = -2046;  // largest e(c0_j) - e(z_j)
   const unsigned long long small_b = pos_bits(0x1p-600);
   int sc_o = 0, sc_n = 0, n = 0;
   const uint32_t e1 = row_ptr[c.i + 1];
@@ -86,12 +88,12 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     if (pos_bits(pz_n) < small_b) { pz_n *= 0x1p600; ++sc_n; }
     if (pos_bits(pz_o) < small_b) { pz_o *= 0x1p600; ++sc_o; }
     bdv += xn - xo;
-    zmin_b = min(zmin_b, min(pos_bits(zn), pos_bits(zo)));
+    dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
     c0s += t.c0;
     ++n;
   }
-  const double lin = n > 0 ? c0s / __longlong_as_double((long long)zmin_b) : 0.0;
-  if (!(lin <= 0x1p-10)) return 2;
+  if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;  // n <= 2^(32 - clz n)
+  const double lin = n > 0 ? ldexp((double)n, dmax + 2) : 0.0;
   double tex = 0.0, bex = 0.0;
   if (P.J != 0.0) {
     double h0 = 0.0, h1 = 0.0, h2 = 0.0;
@@ -287,8 +289,8 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
                                 const double* __restrict__ s,
                                 const uint32_t* __restrict__ row_ptr,
                                 const uint32_t* __restrict__ col, int lane) {
-  double bdv = 0.0, pz_o = 1.0, pz_n = 1.0, zmin = 1.0, c0s = 0.0;
-  int sc_o = 0, sc_n = 0, n = 0, bad = 0;
+  double bdv = 0.0, pz_o = 1.0, pz_n = 1.0, c0s = 0.0;
+  int sc_o = 0, sc_n = 0, n = 0, bad = 0, dmax = -2046;
   const uint32_t e1 = row_ptr[c.i + 1];
   for (uint32_t e = row_ptr[c.i] + lane; e < e1; e += 32) {
     const uint32_t cj = col[e];
@@ -317,7 +319,7 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
     if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
     if (pz_o < 0x1p-600) { pz_o *= 0x1p600; ++sc_o; }
     bdv += xn - xo;
-    zmin = fmin(zmin, fmin(zn, zo));
+    dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
     c0s += t.c0;
     ++n;
   }
@@ -328,12 +330,12 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
   const double labs = warp_sum_d(fabs(lo) + fabs(ln));
   bdv = warp_sum_d(bdv);
   c0s = warp_sum_d(c0s);
-  zmin = warp_min_d(zmin);
+  dmax = __reduce_max_sync(0xffffffffu, dmax);
   n = __reduce_add_sync(0xffffffffu, n);
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (bad) return 2;
-  const double lin = n > 0 ? c0s / zmin : 0.0;
-  if (!(lin <= 0x1p-10)) return 2;
+  if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;
+  const double lin = n > 0 ? ldexp((double)n, dmax + 2) : 0.0;
   double tex = 0.0, bex = 0.0;
   if (P.J != 0.0) {
     double h0 = 0.0, h1 = 0.0, h2 = 0.0;
