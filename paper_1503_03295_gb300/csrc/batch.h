@@ -110,6 +110,9 @@ DevParams make_dev_params(const sco_params& p);
 // Launchers (batch.cu).  Each enqueues one phase for every replica on `st`.
 struct BatchLaunch {
   int kw_schedule;  // 0: all levels in one kernel, buckets by colour; 1: one async kernel per level
+  int kw_low;       // 0: no block-local levels; 1: staged edges; 2: rows at every level
+  int low_grid;     // blocks of the block-local level kernel
+  uint32_t low_ecap;  // its staged-edge capacity per group
   int kw_grid;     // blocks of the persistent KW kernel(s)
   int sweep_grid;  // blocks of the persistent sweep kernel
   unsigned levels;  // KW level launches per colouring (>= every replica's M)
@@ -122,6 +125,9 @@ cudaError_t batch_sweep(const BatchDev& B, const BatchLaunch& L, cudaStream_t st
 cudaError_t batch_step_end(const BatchDev& B, const BatchLaunch& L, cudaStream_t st);
 // co-resident blocks per SM of the two persistent kernels (for the grid sizes)
 int batch_kw_occupancy(int schedule, int R, unsigned pal);
+// blocks per SM of the block-local level kernel and its staged-edge capacity (sets the
+// kernel's shared-memory limit)
+cudaError_t batch_low_setup(int R, int* blocks_per_sm, uint32_t* ecap);
 int batch_sweep_occupancy(int precision, int R);
 size_t batch_sweep_smem(int R);
 

@@ -38,6 +38,8 @@ struct sco_batch {
   int sticky = 0;
   sco_batch_tuning tune{};
   int kw_occ = 1, sweep_occ = 1;
+  int low_occ = 1;        // resident blocks per SM of the block-local level kernel
+  uint32_t low_ecap = 0;  // its staged-edge capacity
   struct Graph {
     cudaGraphExec_t exec;
     int64_t launches;  // kernels in one replay
@@ -138,6 +140,9 @@ cudaError_t alloc_palette(sco_batch* b, uint32_t pal) {
 void set_grids(sco_batch* b) {
   const int sms = num_sms();
   b->L.kw_schedule = b->tune.kw_schedule;
+  b->L.kw_low = b->tune.kw_low;
+  b->L.low_grid = b->low_occ * sms;
+  b->L.low_ecap = b->tune.kw_low == 2 ? 0u : b->low_ecap;
   b->kw_occ = batch_kw_occupancy(b->tune.kw_schedule, b->R, b->B.pal_cap);
   b->L.kw_grid = std::min(b->tune.kw_blocks_per_sm, b->kw_occ) * sms;
   b->L.sweep_grid = std::min(b->tune.sweep_blocks_per_sm, b->sweep_occ) * sms;
@@ -271,7 +276,8 @@ sco_status run_steps(sco_batch* b, int64_t n) {
 bool valid_tuning(const sco_batch_tuning* t) {
   return t && t->steps_per_graph >= 1 && t->steps_per_graph <= 1024 &&
          t->sweep_blocks_per_sm >= 1 && t->kw_blocks_per_sm >= 1 &&
-         (t->use_graph == 0 || t->use_graph == 1) && (t->kw_schedule == 0 || t->kw_schedule == 1);
+         (t->use_graph == 0 || t->use_graph == 1) && (t->kw_schedule == 0 || t->kw_schedule == 1) &&
+         t->kw_low >= 0 && t->kw_low <= 2;
 }
 
 bool same_model(const sco_params& a, const sco_params& b) {
@@ -431,6 +437,9 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return fail(from_cuda(e));
   b->tune.kw_schedule = 0;
+  b->tune.kw_low = 1;
+  if ((e = batch_low_setup(n, &b->low_occ, &b->low_ecap)) != cudaSuccess)
+    return fail(from_cuda(e));
   b->kw_occ = batch_kw_occupancy(0, n, B.pal_cap);
   b->sweep_occ = batch_sweep_occupancy(B.precision, n);
   b->tune.steps_per_graph = 4;
@@ -459,7 +468,7 @@ sco_status sco_batch_set_tuning(sco_batch* b, const sco_batch_tuning* t) {
   SCO_TRY(cudaStreamSynchronize(b->st));
   const bool grids = t->sweep_blocks_per_sm != b->tune.sweep_blocks_per_sm ||
                      t->kw_blocks_per_sm != b->tune.kw_blocks_per_sm ||
-                     t->kw_schedule != b->tune.kw_schedule;
+                     t->kw_schedule != b->tune.kw_schedule || t->kw_low != b->tune.kw_low;
   b->tune = *t;
   b->tune.sweep_blocks_per_sm = std::min(t->sweep_blocks_per_sm, b->sweep_occ);
   if (grids) drop_graphs(b);
@@ -526,6 +535,16 @@ sco_status sco_batch_autotune(sco_batch* b, int32_t trial, sco_batch_tuning* cho
     sco_batch_tuning t = best;
     t.kw_schedule = 1 - best.kw_schedule;
     try_dim({t});
+  }
+  {
+    std::vector<sco_batch_tuning> c;
+    for (int v : {0, 1})
+      if (v != best.kw_low) {
+        sco_batch_tuning t = best;
+        t.kw_low = v;
+        c.push_back(t);
+      }
+    try_dim(c);
   }
   {
     std::vector<sco_batch_tuning> c;

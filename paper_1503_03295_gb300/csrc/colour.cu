@@ -16,10 +16,12 @@
 // cooperative kernel in which every thread recolours its own vertices once their larger
 // neighbours are done: no grid-wide barrier between rounds,
 // same colours as the synchronous rounds, and t_R recovered from the per-vertex rounds.
+#include <algorithm>
 #include <cstdint>
 
 #include "kw_bcr.cuh"
 #include "kw_dev.cuh"
+#include "kw_low.cuh"
 
 namespace sco {
 
@@ -280,6 +282,36 @@ __global__ void k_kw_meta(uint32_t N, uint32_t g, unsigned levels, unsigned long
   plan[0] = RepPlan{g, levels, magic};
 }
 
+// Blocks per SM and staged-edge capacity of the block-local level kernel for groups of gcap
+// vertices (the first call lifts the kernel's shared-memory limit to the device maximum).
+cudaError_t low_setup(uint32_t gcap, int* blocks_per_sm, uint32_t* ecap) {
+  static int s_smem_sm = 0, s_smem_blk = 0;
+  if (s_smem_sm == 0) {
+    int dev = 0, a = 0, b = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&a, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&b, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_kw_low, cudaFuncAttributeMaxDynamicSharedMemorySize, b - 64);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_kw_low, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    s_smem_sm = a;
+    s_smem_blk = b - 64;
+  }
+  int blocks = 1;
+  kw_low_shape(1, gcap, (size_t)s_smem_sm, (size_t)s_smem_blk, &blocks, ecap);
+  int occ = 0;  // what is resident in fact
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &occ, k_kw_low, kLowThreads, kw_low_smem(1, gcap, *ecap));
+  if (e != cudaSuccess) return e;
+  *blocks_per_sm = occ < 1 ? 1 : (occ < blocks ? occ : blocks);
+  return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
@@ -296,11 +328,43 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   ++*launches;
   const unsigned long long ns_limit = 2000000000ull;  // 2 s per wait
   unsigned long long magic = div_magic(g);
+  uint32_t* site_start = reinterpret_cast<uint32_t*>(b.meta);
+  RepPlan* plan = reinterpret_cast<RepPlan*>(b.meta + 2);
+  k_kw_meta<<<1, 1, 0, st>>>((uint32_t)N, g, M, magic, site_start, plan);
+  ++*launches;
+  // levels 1..low: one block per group of g 2^low vertices
+  const unsigned low = kw_low_levels(g, M);
+  if (low > 0) {
+    const uint32_t gcap = g << low;
+    int lbps = 1;
+    uint32_t ecap = 0;
+    if ((e = low_setup(gcap, &lbps, &ecap)) != cudaSuccess) return e;
+    const int64_t groups = (N + ((int64_t)g << low) - 1) / ((int64_t)g << low);
+    const int64_t grid = std::min<int64_t>(groups, (int64_t)lbps * num_sms());
+    KwLowView W{};
+    W.R = 1;
+    W.site_start = site_start;
+    W.plan = plan;
+    W.row_ptr = row_ptr;
+    W.col = col;
+    W.word = b.word;
+    W.cnt = cnt;
+    W.halt = nullptr;
+    W.gcap = gcap;
+    W.ecap = ecap;
+    k_kw_low<<<(unsigned)grid, kLowThreads, kw_low_smem(1, gcap, ecap), st>>>(W);
+    ++*launches;
+  }
   // Large lattices: all levels in one persistent kernel, buckets of equal previous colour in
   // turn (each thread would otherwise own many vertices per level).  Small ones: one kernel
   // per level in which a vertex recolours as soon as its larger neighbours are done (about g
   // grid barriers per level would dominate there).
-  if (N >= (1 << 20) && M > 0 && g <= kBcrMaxPalette && M < kBcrMaxLevels) {
+  if (low >= M) {
+    k_kw_final<<<nb, 256, 0, st>>>(N, M, g, variant, b.word, b.colour, cnt);
+    ++*launches;
+    return cudaGetLastError();
+  }
+  if (N >= (1 << 20) && g <= kBcrMaxPalette && M < kBcrMaxLevels) {
     const size_t sh = kw_bcr_smem(1, g);
     int bps = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_kw_bcr, 256, sh);
@@ -311,10 +375,6 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
         cudaSuccess)
       return e;
     if ((e = cudaMemsetAsync(cnt->bar, 0, sizeof(cnt->bar), st)) != cudaSuccess) return e;
-    uint32_t* site_start = reinterpret_cast<uint32_t*>(b.meta);
-    RepPlan* plan = reinterpret_cast<RepPlan*>(b.meta + 2);
-    k_kw_meta<<<1, 1, 0, st>>>((uint32_t)N, g, M, magic, site_start, plan);
-    ++*launches;
     KwView V{};
     V.R = 1;
     V.site_start = site_start;
@@ -335,6 +395,7 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     V.imeta = b.imeta;
     V.ilist = b.ilist;
     V.gmax = nullptr;
+    V.low_on = 1;
     void* args[] = {(void*)&V};
     e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr, dim3((unsigned)(bps * num_sms())),
                                     dim3(256), args, sh, st);
@@ -353,7 +414,7 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   const int64_t want = (N / 2 + 255) / 256;
   int64_t grid = (int64_t)blocks_per_sm * num_sms();
   if (want < grid) grid = want > 0 ? want : 1;
-  for (unsigned p = 1; p <= M; ++p) {
+  for (unsigned p = low + 1; p <= M; ++p) {
     uint32_t Nn = (uint32_t)N;
     uint32_t gg = g;
     unsigned pp = p;

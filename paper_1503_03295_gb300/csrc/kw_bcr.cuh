@@ -16,6 +16,7 @@
 #include "batch.h"
 #include "grid_dev.cuh"
 #include "kw_dev.cuh"
+#include "kw_low.cuh"
 
 namespace sco {
 namespace {
@@ -47,6 +48,7 @@ struct KwView {
   uint32_t* imeta;
   uint32_t* ilist;
   const unsigned* gmax;         // optional: largest palette on the device (else pal)
+  int low_on;                   // levels 1..kw_low_levels(g, M) already done block-locally
 };
 
 constexpr int kItemList = 8;
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
       const RepPlan pl = V.plan[r];
       const uint32_t N = sbase[r + 1] - sbase[r];
       uint32_t n = 0;
-      if (p <= pl.levels) {
+      if (p <= pl.levels && !(V.low_on && p <= kw_low_levels(pl.g, pl.levels))) {
         const unsigned long long gsz = (unsigned long long)pl.g << p;
         n = (uint32_t)(((unsigned long long)N + gsz - 1) / gsz *
                        ((unsigned long long)pl.g << (p - 1)));
@@ -295,7 +297,10 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
     __syncthreads();
     block_scan_excl(rp, R);
     const uint32_t Rtot = rp[R];
-    if (Rtot == 0) break;
+    if (Rtot == 0) {  // no lattice has this level left (the same in every block)
+      __syncthreads();
+      continue;
+    }
     auto vertex_of = [&](uint32_t slot) -> uint32_t {
       const int r = find_le(rp, R, slot);
       const RepPlan pl = V.plan[r];

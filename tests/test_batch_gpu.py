@@ -80,20 +80,28 @@ def test_results_do_not_depend_on_tuning():
     n = 9
     ref = sco.Batch(ps)
     ref.set_tuning(steps_per_graph=1, sweep_blocks_per_sm=1, kw_blocks_per_sm=1, use_graph=0,
-                   kw_schedule=1)
+                   kw_schedule=1, kw_low=0)
     ref.run(n)
     want = [ref.spins(r) for r in range(len(ps))]
+    want_c = [ref.colours(r) for r in range(len(ps))]
+    want_t = [ref.observables(r)["kw_rounds"] for r in range(len(ps))]
     for t in (dict(steps_per_graph=4, sweep_blocks_per_sm=2, kw_blocks_per_sm=2, use_graph=1),
-              dict(steps_per_graph=3, sweep_blocks_per_sm=6, kw_blocks_per_sm=4, use_graph=1),
-              dict(steps_per_graph=1, sweep_blocks_per_sm=3, kw_blocks_per_sm=1, use_graph=0),
+              dict(steps_per_graph=3, sweep_blocks_per_sm=6, kw_blocks_per_sm=4, use_graph=1,
+                   kw_low=2),
+              dict(steps_per_graph=1, sweep_blocks_per_sm=3, kw_blocks_per_sm=1, use_graph=0,
+                   kw_low=0),
               dict(steps_per_graph=2, sweep_blocks_per_sm=4, kw_blocks_per_sm=2, use_graph=1,
-                   kw_schedule=1)):
+                   kw_schedule=1),
+              dict(steps_per_graph=2, sweep_blocks_per_sm=2, kw_blocks_per_sm=1, use_graph=1,
+                   kw_schedule=1, kw_low=2)):
         with sco.Batch(ps) as b:
             b.set_tuning(**t)
             b.run(4)
             b.run(n - 4)
             for r in range(len(ps)):
                 assert np.array_equal(b.spins(r), want[r]), (t, r)
+                assert np.array_equal(b.colours(r), want_c[r]), (t, r)
+                assert b.observables(r)["kw_rounds"] == want_t[r], (t, r)
     with sco.Batch(ps) as b:
         chosen = b.autotune(trial_steps=1)  # the trial steps are real MC steps
         assert chosen["steps_per_graph"] >= 1
