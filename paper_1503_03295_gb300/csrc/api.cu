@@ -293,6 +293,7 @@ void free_all(sco_ctx* c) {
   cudaFree(c->row_ptr);
   cudaFree(c->col);
   cudaFree(c->cb.word);
+  cudaFree(c->cb.col8);
   cudaFree(c->cb.blk);
   cudaFree(c->cb.colour);
   cudaFree(c->cb.hist);
@@ -370,13 +371,14 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->sw.scan_tmp, scan_tmp_bytes(N + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->row_ptr, (N + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.word, N * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cb.col8, N);
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.blk, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.colour, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.perm, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.meta, 8 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.imask, N * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->cb.imeta, N * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&c->cb.ilist, 8 * N * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cb.ilist, kKwItemList * N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->acc, N);
   if (e == cudaSuccess) e = cudaMalloc(&c->defer, N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->prop, N * sizeof(double4_32a));

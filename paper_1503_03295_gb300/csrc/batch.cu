@@ -224,7 +224,9 @@ __global__ void __launch_bounds__(256) kb_kw_init(const BatchDev B) {
   const uint32_t i = (blockIdx.x - B.blk_start[r]) * kBatchBlock + threadIdx.x;
   if (i >= N) return;
   const RepPlan pl = B.plan[r];
-  B.word[base + i] = pack(0, 0, i - fdiv(i, pl.magic) * pl.g);
+  const uint32_t c = i - fdiv(i, pl.magic) * pl.g;
+  B.word[base + i] = pack(0, 0, c);
+  B.col8[base + i] = (uint8_t)c;
   B.blk[base + i] = kNone;
 }
 
@@ -671,6 +673,7 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
     W.row_ptr = B.row_ptr;
     W.col = B.col;
     W.word = B.word;
+    W.col8 = B.col8;
     W.cnt = B.cnt;
     W.halt = &B.ctl->flag;
     W.gcap = kLowMaxGroup;
@@ -690,6 +693,7 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
     V.row_ptr = B.row_ptr;
     V.col = B.col;
     V.word = B.word;
+    V.col8 = B.col8;
     V.list = B.blk;
     V.bcnt = B.bcnt;
     V.cnt = B.cnt;

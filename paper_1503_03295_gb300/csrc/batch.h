@@ -34,6 +34,9 @@ struct RepDesc {
   int32_t variant;     // colouring variant (reported t_R only)
 };
 
+// Larger right-half neighbours listed per bucketed vertex of the KW colouring (records).
+constexpr int kKwItemList = 32;
+
 // Per-step plan of replica r, written on the device once the graph is known.
 struct RepPlan {
   uint32_t g;       // Delta + 1
@@ -85,6 +88,7 @@ struct BatchDev {
   uint32_t* col;
   unsigned long long col_cap;
   unsigned long long* word;
+  uint8_t* col8;  // colour (low byte) beside the words
   uint32_t* blk;
   uint32_t* colour;
   uint32_t* used;  // R * pal_cap / 32 colour-in-use bits

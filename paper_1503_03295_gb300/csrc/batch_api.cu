@@ -91,6 +91,7 @@ void free_all(sco_batch* b) {
   cudaFree(B.row_ptr);
   cudaFree(B.col);
   cudaFree(B.word);
+  cudaFree(B.col8);
   cudaFree(B.blk);
   cudaFree(B.colour);
   cudaFree(B.used);
@@ -407,6 +408,7 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   B.col_cap = (unsigned long long)N * 24 + 1024;
   A(&B.col, B.col_cap * sizeof(uint32_t));
   A(&B.word, N * sizeof(unsigned long long));
+  A(&B.col8, N);
   A(&B.blk, N * sizeof(uint32_t));
   A(&B.colour, N * sizeof(uint32_t));
   A(&B.perm, N * sizeof(uint32_t));
@@ -414,7 +416,7 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   A(&B.prop, N * sizeof(double4_32a));
   A(&B.imask, N * sizeof(unsigned long long));
   A(&B.imeta, N * sizeof(uint32_t));
-  A(&B.ilist, 8 * N * sizeof(uint32_t));
+  A(&B.ilist, kKwItemList * N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMallocHost(&b->hcnt, n * sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMallocHost(&b->hctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = alloc_palette(b, 256);

@@ -28,10 +28,12 @@ namespace sco {
 namespace {
 
 __global__ void k_kw_init(int64_t N, uint32_t g, unsigned long long* __restrict__ word,
-                          uint32_t* __restrict__ blk) {
+                          uint8_t* __restrict__ col8, uint32_t* __restrict__ blk) {
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v < N) {
-    word[v] = pack(0, 0, (unsigned)(v % g));
+    const unsigned c = (unsigned)(v % g);
+    word[v] = pack(0, 0, c);
+    col8[v] = (uint8_t)c;
     blk[v] = 0xFFFFFFFFu;
   }
 }
@@ -324,7 +326,7 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   cudaError_t e = cudaMemsetAsync(cnt->lev_rounds, 0, sizeof(cnt->lev_rounds), st);
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((N + 255) / 256);
-  k_kw_init<<<nb, 256, 0, st>>>(N, g, b.word, b.blk);
+  k_kw_init<<<nb, 256, 0, st>>>(N, g, b.word, b.col8, b.blk);
   ++*launches;
   const unsigned long long ns_limit = 2000000000ull;  // 2 s per wait
   unsigned long long magic = div_magic(g);
@@ -348,6 +350,7 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     W.row_ptr = row_ptr;
     W.col = col;
     W.word = b.word;
+    W.col8 = b.col8;
     W.cnt = cnt;
     W.halt = nullptr;
     W.gcap = gcap;
@@ -382,6 +385,7 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     V.row_ptr = row_ptr;
     V.col = col;
     V.word = b.word;
+    V.col8 = b.col8;
     V.list = b.blk;
     V.bcnt = b.bcnt;
     V.cnt = cnt;

@@ -31,6 +31,7 @@ struct KwView {
   const uint32_t* row_ptr;      // global entry offsets; col entries lattice-local
   const uint32_t* col;
   unsigned long long* word;     // packed (level, round, colour), global vertex index
+  uint8_t* col8;                // colour (low byte) beside the words (null: words only)
   uint32_t* list;               // bucketed right-half vertices of the current level
   uint32_t* bcnt;               // kBcrMaxLevels x pal bucket sizes, zero on entry
   DevCounters* cnt;             // R: lev_rounds
@@ -51,7 +52,8 @@ struct KwView {
   int low_on;                   // levels 1..kw_low_levels(g, M) already done block-locally
 };
 
-constexpr int kItemList = 8;
+constexpr int kItemList = kKwItemList;
+constexpr int kItemChunk = 16;  // listed neighbours loaded together
 constexpr uint32_t kItemSlow = 0x100;
 
 __device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t* p) {
@@ -74,25 +76,24 @@ __device__ __forceinline__ void kw_item_build(const KwView& V, uint32_t pos, uin
   const uint32_t v = gv - base;
   const uint32_t grp = fdiv(v, M) >> p;
   const uint32_t b = V.row_ptr[gv], e = V.row_ptr[gv + 1];
-  const unsigned long long* word = V.word + base;
+  const uint8_t* col8 = V.col8 + base;
   unsigned long long mask = 0;
   uint32_t n = 0;
   uint32_t* out = V.ilist + (size_t)pos * kItemList;
   for (uint32_t q0 = b; q0 < e; q0 += 16) {
-    uint32_t uu[16];
-    unsigned long long ww[16];
+    uint32_t uu[16], cc[16];
 #pragma unroll
     for (int a = 0; a < 16; ++a) uu[a] = q0 + a < e ? (V.col[q0 + a] & kIndexMask) : kNone;
 #pragma unroll
     for (int a = 0; a < 16; ++a) {
-      ww[a] = 0;
-      if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) ww[a] = ld_relaxed(&word[uu[a]]);
+      cc[a] = 0;
+      if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) cc[a] = ld_relaxed_u8(&col8[uu[a]]);
       else uu[a] = kNone;
     }
 #pragma unroll
     for (int a = 0; a < 16; ++a) {
       if (uu[a] == kNone) continue;
-      const uint32_t cu = (uint32_t)(ww[a] & kColMask);
+      const uint32_t cu = cc[a];
       if (!((fdiv(uu[a], M) >> (p - 1)) & 1u)) {
         mask |= 1ull << (cu & 63);
       } else if (cu > c) {
@@ -105,60 +106,67 @@ __device__ __forceinline__ void kw_item_build(const KwView& V, uint32_t pos, uin
   V.imeta[pos] = n > (uint32_t)kItemList ? kItemSlow : n;
 }
 
-// An item's record, loaded ahead of its bucket.
+// An item's record head, loaded ahead of its bucket (the list is read when it runs).
 struct KwItem {
   uint32_t gv;    // global vertex (kNone: no item)
   uint32_t meta;  // listed neighbours, or kItemSlow
+  uint32_t pos;   // record index
   unsigned long long mask;
-  uint32_t u[kItemList];
 };
 
 __device__ __forceinline__ void kw_item_fetch(KwItem& it, const KwView& V, uint32_t pos) {
+  it.pos = pos;
   it.gv = ld_u32_gpu(&V.list[pos]);
   it.meta = ld_u32_gpu(&V.imeta[pos]);
   it.mask = ld_relaxed(&V.imask[pos]);
-  const uint32_t* src = V.ilist + (size_t)pos * kItemList;
-#pragma unroll
-  for (int a = 0; a < kItemList; a += 4) {
-    const uint4 x = ld_relaxed_v4(src + a);
-    it.u[a] = x.x;
-    it.u[a + 1] = x.y;
-    it.u[a + 2] = x.z;
-    it.u[a + 3] = x.w;
-  }
 }
 
 // Recolours an item from its record: the listed neighbours are final (bounded wait otherwise,
 // which the bucket order rules out); new colour = smallest one free of mask and their
-// colours, round = 1 + their largest round.
+// colours, round = 1 + their largest round.  The list is read kItemChunk entries at a time,
+// then their words together.
 __device__ __forceinline__ bool kw_item_recolour(const KwItem& it, const KwView& V, unsigned p,
                                                  unsigned& rmax, unsigned long long t_start) {
   const uint32_t n = it.meta;
-  unsigned long long ww[kItemList];
-#pragma unroll
-  for (int a = 0; a < kItemList; ++a) ww[a] = (uint32_t)a < n ? ld_relaxed(&V.word[it.u[a]]) : 0;
+  const uint32_t* src = V.ilist + (size_t)it.pos * kItemList;
   unsigned long long mask = it.mask;
   unsigned rv = 0;
+  for (uint32_t a0 = 0; a0 < n; a0 += kItemChunk) {
+    uint32_t u[kItemChunk];
 #pragma unroll
-  for (int a = 0; a < kItemList; ++a) {
-    if ((uint32_t)a >= n) continue;
-    unsigned long long wu = ww[a];
-    unsigned spins = 0;
-    while (tag_of(wu) != p) {
-      __nanosleep(64);
-      wu = ld_relaxed(&V.word[it.u[a]]);
-      if ((++spins & 255) == 0 &&
-          (global_ns() - t_start > V.ns_limit || ld_status(V.status) != 0)) {
-        atomicCAS(V.status, 0, kStatusTimeout);
-        return false;
-      }
+    for (int a = 0; a < kItemChunk; a += 4) {
+      uint4 x = make_uint4(0, 0, 0, 0);
+      if (a0 + a < n) x = ld_relaxed_v4(src + a0 + a);
+      u[a] = x.x;
+      u[a + 1] = x.y;
+      u[a + 2] = x.z;
+      u[a + 3] = x.w;
     }
-    mask |= 1ull << ((uint32_t)(wu & kColMask) & 63);
-    rv = max(rv, rnd_of(wu));
+    unsigned long long ww[kItemChunk];
+#pragma unroll
+    for (int a = 0; a < kItemChunk; ++a) ww[a] = a0 + a < n ? ld_relaxed(&V.word[u[a]]) : 0;
+#pragma unroll
+    for (int a = 0; a < kItemChunk; ++a) {
+      if (a0 + a >= n) continue;
+      unsigned long long wu = ww[a];
+      unsigned spins = 0;
+      while (tag_of(wu) != p) {
+        __nanosleep(64);
+        wu = ld_relaxed(&V.word[u[a]]);
+        if ((++spins & 255) == 0 &&
+            (global_ns() - t_start > V.ns_limit || ld_status(V.status) != 0)) {
+          atomicCAS(V.status, 0, kStatusTimeout);
+          return false;
+        }
+      }
+      mask |= 1ull << ((uint32_t)(wu & kColMask) & 63);
+      rv = max(rv, rnd_of(wu));
+    }
   }
   const unsigned cn = (unsigned)(__ffsll((long long)~mask) - 1);
   rmax = max(rmax, rv + 1);
   st_relaxed(&V.word[it.gv], pack(p, rv + 1, cn));
+  st_relaxed_u8(&V.col8[it.gv], cn);
   return true;
 }
 
@@ -187,8 +195,9 @@ __device__ __forceinline__ void kw_fetch(KwRow& w, uint32_t gv, const uint32_t* 
 __device__ __forceinline__ bool kw_recolour(uint32_t v, uint32_t c, const KwRow& w, unsigned p,
                                             unsigned long long M,
                                             const uint32_t* __restrict__ col,
-                                            unsigned long long* word, unsigned& rmax,
-                                            int* status, unsigned long long t_start,
+                                            unsigned long long* word, uint8_t* col8,
+                                            unsigned& rmax, int* status,
+                                            unsigned long long t_start,
                                             unsigned long long ns_limit) {
   const uint32_t grp = fdiv(v, M) >> p;
   const uint32_t b = w.b, e = w.e;
@@ -247,6 +256,7 @@ __device__ __forceinline__ bool kw_recolour(uint32_t v, uint32_t c, const KwRow&
   }
   rmax = max(rmax, rv + 1);
   st_relaxed(&word[v], pack(p, rv + 1, cn));
+  if (col8) st_relaxed_u8(&col8[v], cn);
   return true;
 }
 
@@ -274,7 +284,7 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
   const uint32_t nth = gridDim.x * blockDim.x;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
   // records (instead of rows) when every palette fits a 64-bit mask
-  const bool fast = V.imask != nullptr && (V.gmax ? *V.gmax : pal) <= 64u;
+  const bool fast = V.imask != nullptr && V.col8 != nullptr && (V.gmax ? *V.gmax : pal) <= 64u;
   bool ok = true;
   for (unsigned p = 1; p <= V.levels && ok; ++p) {
     // right-half slots of every lattice at level p
@@ -311,7 +321,10 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
     // bucket sizes: block histograms, then one reservation per (block, colour)
     for (uint32_t slot = gtid; slot < Rtot; slot += nth) {
       const uint32_t gv = vertex_of(slot);
-      if (gv != kNone) atomicAdd(&hist[(uint32_t)(ld_relaxed(&V.word[gv]) & kColMask)], 1u);
+      if (gv != kNone)
+        atomicAdd(&hist[fast ? ld_relaxed_u8(&V.col8[gv])
+                             : (uint32_t)(ld_relaxed(&V.word[gv]) & kColMask)],
+                  1u);
     }
     __syncthreads();
     for (unsigned c = threadIdx.x; c < pal; c += blockDim.x)
@@ -326,7 +339,8 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
     for (uint32_t slot = gtid; slot < Rtot; slot += nth) {
       const uint32_t gv = vertex_of(slot);
       if (gv == kNone) continue;
-      const uint32_t c = (uint32_t)(ld_relaxed(&V.word[gv]) & kColMask);
+      const uint32_t c =
+          fast ? ld_relaxed_u8(&V.col8[gv]) : (uint32_t)(ld_relaxed(&V.word[gv]) & kColMask);
       const uint32_t pos = start[c] + offb[c] + atomicAdd(&lcur[c], 1u);
       V.list[pos] = gv;
       if (fast) {
@@ -364,7 +378,7 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
             KwRow w;
             kw_fetch(w, it.gv, V.row_ptr, V.col);
             mine = kw_recolour(it.gv - base, (uint32_t)c, w, p, V.plan[r].magic, V.col,
-                               V.word + base, rm, V.status, t_start, V.ns_limit);
+                               V.word + base, V.col8 + base, rm, V.status, t_start, V.ns_limit);
           } else {
             mine = kw_item_recolour(it, V, p, rm, t_start);
           }
@@ -392,7 +406,7 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
           const uint32_t base = sbase[r];
           unsigned rm = 0;
           mine = kw_recolour(gv - base, (uint32_t)c, w, p, V.plan[r].magic, V.col, V.word + base,
-                             rm, V.status, t_start, V.ns_limit);
+                             nullptr, rm, V.status, t_start, V.ns_limit);
           atomicMax(&smax[r], rm);
         }
         grid_arrive(V.bar, s_old);

@@ -43,6 +43,7 @@ struct KwLowView {
   const uint32_t* row_ptr;      // global entry offsets; col entries lattice-local
   const uint32_t* col;
   unsigned long long* word;     // packed (level, round, colour), global vertex index
+  uint8_t* col8;                // colour (low byte), global vertex index
   DevCounters* cnt;             // R: lev_rounds
   const int* halt;              // optional: nonzero on entry -> return at once
   uint32_t gcap;                // >= every group size g 2^p0, <= kLowMaxGroup, even
@@ -371,11 +372,13 @@ __global__ void __launch_bounds__(kLowThreads) k_kw_low(const KwLowView V) {
     // words: colour, round at the last recolouring, and that level (the highest of the
     // first p0 levels at which the vertex was in a right half; 0 if none)
     unsigned long long* word = V.word + base + v0;
+    uint8_t* col8 = V.col8 + base + v0;
     for (uint32_t l = tid; l < n; l += T) {
       const uint32_t s = st[l];
       const uint32_t bits = low_div(l, m32) & ((1u << low) - 1u);
       const uint32_t tag = bits ? 32u - (uint32_t)__clz((int)bits) : 0u;
       word[l] = pack(tag, tag ? (s >> 6) & 0x7Fu : 0u, s & 63u);
+      col8[l] = (uint8_t)(s & 63u);
     }
     if (tid >= 1 && tid <= low && rl[tid]) atomicMax(&V.cnt[r].lev_rounds[tid & 31], rl[tid]);
     __syncthreads();  // shared memory is reused by the next group

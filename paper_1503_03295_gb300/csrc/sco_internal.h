@@ -92,6 +92,7 @@ cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* ro
 // ---- colour.cu ----
 struct ColourBufs {
   unsigned long long* word;  // N packed (level tag, round, colour)
+  uint8_t* col8;     // N colour (low byte), kept beside the words for the neighbour gathers
   uint32_t* blk;     // N neighbour each unfinished vertex waits for (0xFFFFFFFF: none)
   uint32_t* colour;  // N final colours
   uint32_t* hist;    // g + 1
