@@ -72,9 +72,11 @@ __device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t* p) {
 // of at most 64 colours.
 __device__ __forceinline__ void kw_item_build(const KwView& V, uint32_t pos, uint32_t gv,
                                               uint32_t base, uint32_t c, unsigned p,
-                                              unsigned long long M) {
+                                              const RepPlan& pl) {
   const uint32_t v = gv - base;
-  const uint32_t grp = fdiv(v, M) >> p;
+  // v's level-p group is [lo, lo + gsz), its left half [lo, lo + half)
+  const uint32_t gsz = pl.g << p, half = pl.g << (p - 1);
+  const uint32_t lo = (fdiv(v, pl.magic) >> p) * gsz;
   const uint32_t b = V.row_ptr[gv], e = V.row_ptr[gv + 1];
   const uint8_t* col8 = V.col8 + base;
   unsigned long long mask = 0;
@@ -85,19 +87,19 @@ __device__ __forceinline__ void kw_item_build(const KwView& V, uint32_t pos, uin
 #pragma unroll
     for (int a = 0; a < 16; ++a) uu[a] = q0 + a < e ? (V.col[q0 + a] & kIndexMask) : kNone;
 #pragma unroll
-    for (int a = 0; a < 16; ++a) {
+    for (int a = 0; a < 16; ++a) {  // offsets inside the group (>= gsz: another group)
       cc[a] = 0;
-      if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) cc[a] = ld_relaxed_u8(&col8[uu[a]]);
-      else uu[a] = kNone;
+      uu[a] = uu[a] - lo;
+      if (uu[a] < gsz) cc[a] = ld_relaxed_u8(&col8[lo + uu[a]]);
     }
 #pragma unroll
     for (int a = 0; a < 16; ++a) {
-      if (uu[a] == kNone) continue;
+      if (uu[a] >= gsz) continue;
       const uint32_t cu = cc[a];
-      if (!((fdiv(uu[a], M) >> (p - 1)) & 1u)) {
+      if (uu[a] < half) {
         mask |= 1ull << (cu & 63);
       } else if (cu > c) {
-        if (n < (uint32_t)kItemList) out[n] = base + uu[a];
+        if (n < (uint32_t)kItemList) out[n] = base + lo + uu[a];
         ++n;
       }
     }
@@ -193,13 +195,15 @@ __device__ __forceinline__ void kw_fetch(KwRow& w, uint32_t gv, const uint32_t* 
 // (which the bucket order rules out) would be waited for, bounded (false on timeout or
 // error).  Neighbour words are loaded sixteen at a time, back to back.
 __device__ __forceinline__ bool kw_recolour(uint32_t v, uint32_t c, const KwRow& w, unsigned p,
-                                            unsigned long long M,
+                                            uint32_t g, unsigned long long M,
                                             const uint32_t* __restrict__ col,
                                             unsigned long long* word, uint8_t* col8,
                                             unsigned& rmax, int* status,
                                             unsigned long long t_start,
                                             unsigned long long ns_limit) {
-  const uint32_t grp = fdiv(v, M) >> p;
+  // v's level-p group is [lo, lo + gsz), its left half [lo, lo + half)
+  const uint32_t gsz = g << p, half = g << (p - 1);
+  const uint32_t lo = (fdiv(v, M) >> p) * gsz;
   const uint32_t b = w.b, e = w.e;
   unsigned long long used[4] = {0, 0, 0, 0};  // colours < 256 (mex <= degree)
   unsigned rv = 0;
@@ -214,22 +218,22 @@ __device__ __forceinline__ bool kw_recolour(uint32_t v, uint32_t c, const KwRow&
       for (int a = 0; a < 16; ++a) uu[a] = q0 + a < e ? (col[q0 + a] & kIndexMask) : kNone;
     }
 #pragma unroll
-    for (int a = 0; a < 16; ++a) {
+    for (int a = 0; a < 16; ++a) {  // offsets inside the group (>= gsz: another group)
       ww[a] = 0;
-      if (uu[a] != kNone && (fdiv(uu[a], M) >> p) == grp) ww[a] = ld_relaxed(&word[uu[a]]);
-      else uu[a] = kNone;
+      uu[a] = uu[a] - lo;
+      if (uu[a] < gsz) ww[a] = ld_relaxed(&word[lo + uu[a]]);
     }
 #pragma unroll
     for (int a = 0; a < 16; ++a) {
-      if (uu[a] == kNone) continue;
+      if (uu[a] >= gsz) continue;
       unsigned long long wu = ww[a];
-      const bool right = (fdiv(uu[a], M) >> (p - 1)) & 1u;
+      const bool right = uu[a] >= half;
       if (right && tag_of(wu) != p) {
         if ((uint32_t)(wu & kColMask) < c) continue;  // smaller: still >= g
         unsigned spins = 0;
         while (tag_of(wu) != p) {
           __nanosleep(64);
-          wu = ld_relaxed(&word[uu[a]]);
+          wu = ld_relaxed(&word[lo + uu[a]]);
           if ((++spins & 255) == 0 &&
               (global_ns() - t_start > ns_limit || ld_status(status) != 0)) {
             atomicCAS(status, 0, kStatusTimeout);
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
       V.list[pos] = gv;
       if (fast) {
         const int r = find_le(sbase, R, gv);
-        kw_item_build(V, pos, gv, sbase[r], c, p, V.plan[r].magic);
+        kw_item_build(V, pos, gv, sbase[r], c, p, V.plan[r]);
       }
     }
     if (!grid_sync(V.bar, V.status, V.ns_limit)) {
@@ -377,8 +381,9 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
             const uint32_t base = sbase[r];
             KwRow w;
             kw_fetch(w, it.gv, V.row_ptr, V.col);
-            mine = kw_recolour(it.gv - base, (uint32_t)c, w, p, V.plan[r].magic, V.col,
-                               V.word + base, V.col8 + base, rm, V.status, t_start, V.ns_limit);
+            mine = kw_recolour(it.gv - base, (uint32_t)c, w, p, V.plan[r].g, V.plan[r].magic,
+                               V.col, V.word + base, V.col8 + base, rm, V.status, t_start,
+                               V.ns_limit);
           } else {
             mine = kw_item_recolour(it, V, p, rm, t_start);
           }
@@ -405,8 +410,8 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
           const int r = find_le(sbase, R, gv);
           const uint32_t base = sbase[r];
           unsigned rm = 0;
-          mine = kw_recolour(gv - base, (uint32_t)c, w, p, V.plan[r].magic, V.col, V.word + base,
-                             nullptr, rm, V.status, t_start, V.ns_limit);
+          mine = kw_recolour(gv - base, (uint32_t)c, w, p, V.plan[r].g, V.plan[r].magic, V.col,
+                             V.word + base, nullptr, rm, V.status, t_start, V.ns_limit);
           atomicMax(&smax[r], rm);
         }
         grid_arrive(V.bar, s_old);
