@@ -157,13 +157,25 @@ class ClockSampler:
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal
 # DRAM bytes (read + write) of one FP64 sweep launch (one colour class) at L=2304, T=0.6D,
 # seed 0, from one ncu capture (profiles/dram_traffic_L2304_T0.6.md); valid for that workload
-SWEEP64_TRAFFIC_PER_CLASS = 73.3e6
+SWEEP64_TRAFFIC_PER_CLASS = 95.5e6
 
 
-def algorithmic_bytes(k, M):
+def low_levels(g, M):
+    """KW levels taken block-locally (groups of g 2^p <= 4096 vertices, palettes <= 64)."""
+    p = 0
+    if g <= 64:
+        while p < M and (g << (p + 1)) <= 4096:
+            p += 1
+    return p
+
+
+def algorithmic_bytes(k, M, p0):
     """Bytes per spin update that each phase must move at least once:
-    switch + CSR 40 + 16k, colouring + classes M (4 + 2k) + 12, sweep 60 + 8k."""
-    return {"switch": 40 + 16 * k, "colour": M * (4 + 2 * k) + 12, "sweep": 60 + 8 * k}
+    switch + CSR 40 + 16k; colouring + classes: the first p0 levels read the rows once and write
+    the colours (4 + 4k + 9), every later level half the rows and colours (4 + 2k), classes 12;
+    sweep 60 + 8k."""
+    colour = (4 + 4 * k + 9 if p0 else 0) + (M - p0) * (4 + 2 * k) + 12
+    return {"switch": 40 + 16 * k, "colour": colour, "sweep": 60 + 8 * k}
 
 
 def algorithmic_flops(k, cand):
@@ -179,9 +191,9 @@ def phase_ms(ph):
             "sweep": ph["sweep_ms"] / max(ph["sweep_calls"], 1)}
 
 
-def rooflines(per_step, N, k, M, cand, hbm, how, fp64):
+def rooflines(per_step, N, k, M, p0, cand, hbm, how, fp64):
     """HBM roofline of every phase and, for the FP64 form, the FP64-ALU roofline."""
-    ab = algorithmic_bytes(k, M)
+    ab = algorithmic_bytes(k, M, p0)
     af = algorithmic_flops(k, cand)
     out = {}
     for ph, ms in per_step.items():
@@ -390,7 +402,8 @@ def main():
     cand = CANDIDATES_PER_SITE.get(round(args.T, 3), 14.4)
     hbm, how = peaks()
     per_step = phase_ms(f64["phases"])
-    roof = rooflines(per_step, N, k, levels, cand, hbm, how, True)
+    p0 = low_levels(g, levels)
+    roof = rooflines(per_step, N, k, levels, p0, cand, hbm, how, True)
     dom = max(per_step, key=per_step.get)
     if roof[dom].get("fp64_achieved_GFLOPs"):
         traffic = None
@@ -421,7 +434,7 @@ def main():
         "phases_ms_per_step": per_step,
         "graph": {"mean_degree": k, "max_degree": obs["max_degree"],
                   "n_colours": obs["n_colours"], "kw_rounds": obs["kw_rounds"],
-                  "kw_levels": levels},
+                  "kw_levels": levels, "kw_block_local_levels": p0},
         "roofline": primary,
         "roofline_phases": roof,
     }
@@ -433,7 +446,7 @@ def main():
         line["fp32_guarded"] = {
             "value": whole_job_rate(N, K, world, f32["ms"]), "ms_per_step": f32["ms"] / K,
             "gpu_launches": f32["launches"], "phases_ms_per_step": p32,
-            "roofline_phases": rooflines(p32, N, k, levels, cand, hbm, how, False),
+            "roofline_phases": rooflines(p32, N, k, levels, p0, cand, hbm, how, False),
             "guard_hits_fp32": f32["obs"]["guard_hits_fp32"],
             "guard_hits_fp64": f32["obs"]["guard_hits_fp64"]}
     if "batch" in res:
