@@ -242,7 +242,7 @@ sco_status sco_batch_info(sco_batch* b, int64_t* total_sites, int64_t* steps_don
 sco_status sco_batch_sync(sco_batch* b);
 
 /* Self-test of the library's own elementary function: the branch-free expm1 for x <= 0.35 used
- * by the FP64 decisions of the switch and the sweep (argument reduction by ln 2, a degree-8
+ * by the FP64 decisions of the switch (argument reduction by ln 2, a degree-8
  * polynomial on |r| <= 0.35, -1 below x = -40), stated relative error bound 2^-42, which those
  * decisions carry in their error bounds.  Evaluates it at n >= 17 points of [-50, 0.35] (16
  * fixed points, then Philox-jittered evenly spaced ones from `seed`) and returns the largest
@@ -251,6 +251,12 @@ sco_status sco_batch_sync(sco_batch* b);
  * counterpart in the paper. */
 sco_status sco_selftest_expm1(int64_t n, uint64_t seed, double* max_rel_err,
                               double* max_rel_diff_cuda);
+
+/* The same for either degree of the polynomial: degree 8 (the one above, used by the switch)
+ * or degree 6 (used by the sweep decisions, stated relative error bound 2^-31).  Any other
+ * degree: SCO_EINVAL. */
+sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t degree, double* max_rel_err,
+                                  double* max_rel_diff_cuda);
 
 /* Waits for the context's stream; returns the sticky device status. */
 sco_status sco_sync(sco_ctx* c);

@@ -106,6 +106,8 @@ def load():
         "sco_batch_info": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                             C.POINTER(C.c_int64), C.POINTER(C.c_int32)], st),
         "sco_batch_sync": ([vp], st),
+        "sco_selftest_expm1_deg": ([C.c_int64, C.c_uint64, C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)], st),
         "sco_selftest_expm1": ([C.c_int64, C.c_uint64, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)], st),
     }
@@ -144,12 +146,12 @@ def kw_colour_static(row_ptr_dev, col_dev, n, colour_dev, variant=0, stream=None
     return d.value, r.value
 
 
-def selftest_expm1(n=1 << 24, seed=1):
-    """Largest relative error of the library's expm1 (x <= 0.35) against double-double and
-    against CUDA's expm1 (see sco_selftest_expm1)."""
+def selftest_expm1(n=1 << 24, seed=1, degree=8):
+    """Largest relative error of the library's expm1 (x <= 0.35; polynomial degree 8 or 6)
+    against double-double and against CUDA's expm1 (see sco_selftest_expm1_deg)."""
     a, b = C.c_double(), C.c_double()
-    _check(load().sco_selftest_expm1(int(n), int(seed), C.byref(a), C.byref(b)),
-           "sco_selftest_expm1")
+    _check(load().sco_selftest_expm1_deg(int(n), int(seed), int(degree), C.byref(a), C.byref(b)),
+           "sco_selftest_expm1_deg")
     return a.value, b.value
 
 

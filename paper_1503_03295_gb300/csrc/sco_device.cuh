@@ -142,18 +142,26 @@ __device__ __forceinline__ double pair_V(double Dc, double r2, double ax, double
 // these while |expm1(x)| >= 0.29.  Stated as kExpm1RelErr = 2^-42; the FP64 decisions carry it
 // in their error bounds.
 constexpr double kExpm1RelErr = 0x1p-42;
-__device__ __forceinline__ double expm1_np(double x) {
+// The same with p of degree 6 (expm1_poly6, interpolation error < 2.9e-10): relative error below
+// 2^-31.6 by the same argument; stated as kExpm1RelErr6 = 2^-31.  For the sweep decisions, whose
+// bound adds these errors relatively (the switch's survival margin is absolute and keeps the
+// accurate one: next to the thinning bound of a far pair it must stay small).
+constexpr double kExpm1RelErr6 = 0x1p-31;
+template <int kDeg>
+__device__ __forceinline__ double expm1_np_deg(double x) {
   const double t = fma(x, kExpInvLn2, 0x1.8p52);
   const double kd = t - 0x1.8p52;
   const int k = max(__double2loint(t), -1000);
   const double r = fma(-kd, kExpLn2, x);
-  const double e = r * expm1_poly(r);
+  const double e = r * (kDeg == 8 ? expm1_poly(r) : expm1_poly6(r));
   const double s = __longlong_as_double((long long)(1023 + k) << 52);
   const double res = fma(s, e, s - 1.0);
   // x < -40 from the bits: sign set and |x| bits above those of 40
   const long long xb = __double_as_longlong(x);
   return (xb < 0 && (xb & 0x7FFFFFFFFFFFFFFFll) > 0x4044000000000000ll) ? -1.0 : res;
 }
+__device__ __forceinline__ double expm1_np(double x) { return expm1_np_deg<8>(x); }
+__device__ __forceinline__ double expm1_np6(double x) { return expm1_np_deg<6>(x); }
 
 // Sweep constants of a pair at (|dx|, |dy|) for the FP64 decisions (64 bytes).  With the
 // signs of (dx, dy) applied to a3x, a3y, ax, ay, the field of S_j on site i scaled by beta is

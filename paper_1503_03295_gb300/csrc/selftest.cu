@@ -1,6 +1,7 @@
-// selftest.cu -- device self-test of the library's own elementary function expm1_np (the expm1
-// used by the FP64 decisions): its relative error against the double-double expm1 and its
-// difference from the CUDA expm1, on points spread over [-50, 0.35].
+// selftest.cu -- device self-test of the library's own elementary function expm1 (the degree-8
+// expm1_np of the FP64 switch, the degree-6 expm1_np6 of the FP64 sweep decisions): its relative
+// error against the double-double expm1 and its difference from the CUDA expm1, on points
+// spread over [-50, 0.35].
 #include <cstdint>
 #include <cstring>
 
@@ -16,6 +17,7 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) 
 
 // Point k of n: fixed points (range ends, the -40 switch, reduction boundaries, tiny values),
 // then n - 16 evenly spaced points of [-50, 0.35] each moved by a Philox fraction of the step.
+template <int kDeg>
 __global__ void k_expm1_test(int64_t n, uint64_t seed, dd ln2, unsigned long long* out) {
   const double fixed[16] = {-50.0,       -40.0,         -39.999999999, -0.34657359027997264,
                             -0.34657359027997270, -0.6931471805599453, -1.0397207708399179,
@@ -32,7 +34,7 @@ __global__ void k_expm1_test(int64_t n, uint64_t seed, dd ln2, unsigned long lon
       x = -50.0 + 50.35 * ((double)(k - 16) + u53(w.w[0])) / (double)(n - 16);
     }
     if (x == 0.0) continue;
-    const double y = expm1_np(x);
+    const double y = expm1_np_deg<kDeg>(x);
     const dd r = dd_expm1(dd_from(x), ln2);
     const dd d = dd_sub(dd_from(y), r);
     e_dd = fmax(e_dd, fabs(d.hi / r.hi));
@@ -48,9 +50,9 @@ __global__ void k_expm1_test(int64_t n, uint64_t seed, dd ln2, unsigned long lon
 
 using namespace sco;
 
-extern "C" sco_status sco_selftest_expm1(int64_t n, uint64_t seed, double* max_rel_err,
-                                         double* max_rel_diff_cuda) {
-  if (n < 17 || !max_rel_err) return SCO_EINVAL;
+extern "C" sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t degree,
+                                             double* max_rel_err, double* max_rel_diff_cuda) {
+  if (n < 17 || !max_rel_err || (degree != 6 && degree != 8)) return SCO_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SCO_ECUDA;
   unsigned long long* d = nullptr;
@@ -66,7 +68,8 @@ extern "C" sco_status sco_selftest_expm1(int64_t n, uint64_t seed, double* max_r
   }
   const dd ln2 = dd_ldexp(sum, 1);
   if (e == cudaSuccess) {
-    k_expm1_test<<<1024, 256>>>(n, seed, ln2, d);
+    if (degree == 8) k_expm1_test<8><<<1024, 256>>>(n, seed, ln2, d);
+    else k_expm1_test<6><<<1024, 256>>>(n, seed, ln2, d);
     e = cudaGetLastError();
   }
   unsigned long long h[2] = {0, 0};
@@ -79,4 +82,9 @@ extern "C" sco_status sco_selftest_expm1(int64_t n, uint64_t seed, double* max_r
   *max_rel_err = a;
   if (max_rel_diff_cuda) *max_rel_diff_cuda = b;
   return SCO_OK;
+}
+
+extern "C" sco_status sco_selftest_expm1(int64_t n, uint64_t seed, double* max_rel_err,
+                                         double* max_rel_diff_cuda) {
+  return sco_selftest_expm1_deg(n, seed, 8, max_rel_err, max_rel_diff_cuda);
 }

@@ -48,8 +48,8 @@ constexpr int kScale32 = 60;
 //   operations; it must stay below 2^-10 or the decision is left undecided.
 
 // FP64 decision (0: reject, 1: accept, 2: undecided).  eps_r = 2^-52 (unit roundoff, with
-// margin), eps_f = 2^-50 for the CUDA logarithms (within 4 ulp), eps_z = kExpm1RelErr for the
-// library's expm1_np (two per pair, doubled: 4 eps_z).  Compares, minima and renormalisation
+// margin), eps_f = 2^-50 for the CUDA logarithms (within 4 ulp), eps_z = kExpm1RelErr6 for the
+// library's expm1_np6 (two per pair, doubled: 4 eps_z).  Compares, minima and renormalisation
 // tests work on the bits of positive doubles (integer pipe).
 __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
                                            const Sw64* __restrict__ sw,
@@ -82,7 +82,7 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     const double xn = (N0 * gx + N1 * gy + N2 * gz) - bvm;
     const double xo = (S0 * gx + S1 * gy + S2 * gz) - bvm;
     if (!neg_strict(xn) || !neg_strict(xo)) return 2;
-    const double zn = -expm1_np(xn), zo = -expm1_np(xo);
+    const double zn = -expm1_np6(xn), zo = -expm1_np6(xo);
     pz_n *= zn;
     pz_o *= zo;
     if (pos_bits(pz_n) < small_b) { pz_n *= 0x1p600; ++sc_n; }
@@ -115,7 +115,7 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
   const double scale = (double)((sc_n - sc_o) * kScale64) * P.ln2_hi;
   const double lu = log(c.u);
   const double mu = lu + ((bdv + tex) + ((lo - ln) + scale));
-  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr + 0x1p-51) +
+  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
                           0x1p-50 * (fabs(lo) + fabs(ln) + fabs(lu)) + bex +
                           0x1p-51 * (fabs(scale) + fabs(tex) + fabs(bdv) + fabs(mu)));
   if (mu < -B) return 1;
@@ -313,7 +313,7 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
       bad = 1;
       continue;
     }
-    const double zn = -expm1_np(xn), zo = -expm1_np(xo);
+    const double zn = -expm1_np6(xn), zo = -expm1_np6(xo);
     pz_n *= zn;
     pz_o *= zo;
     if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
@@ -354,7 +354,7 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
   }
   const double lu = log(c.u);
   const double mu = lu + ((bdv + tex) + lsum);
-  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr + 0x1p-51) +
+  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
                           0x1p-50 * (labs + fabs(lu)) + 0x1p-49 * labs + bex +
                           0x1p-51 * (fabs(tex) + fabs(bdv) + fabs(mu)));
   if (mu < -B) return 1;

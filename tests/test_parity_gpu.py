@@ -203,3 +203,7 @@ def test_library_expm1_within_its_bound():
     err, diff = sco.selftest_expm1(1 << 24, seed=3)
     assert err < 2.0 ** -42
     assert diff < 2.0 ** -42
+    # the degree-6 variant of the sweep decisions, stated bound 2^-31
+    err, diff = sco.selftest_expm1(1 << 24, seed=4, degree=6)
+    assert err < 2.0 ** -31
+    assert diff < 2.0 ** -31
