@@ -153,3 +153,23 @@ def test_set_spins_roundtrip_and_errors():
         with pytest.raises(sco.ScoError) as e:
             b.graph(0)  # no graph before the first step
         assert e.value.status == sco.SCO_ESTATE
+
+
+@pytest.mark.slow
+def test_batched_workload_64_replicas():
+    """The batched workload itself: 64 replicas (L in {64, 128, 256, 512} x 16 temperatures in
+    [0.2, 1.5] D), FP32-guarded, autotuned; after its steps, sampled replicas of every size
+    (lowest and highest T) equal their single-lattice runs, and one small one the oracle."""
+    ps = sco.replica_params()
+    with sco.Batch(ps) as b:
+        b.autotune(trial_steps=1)
+        b.run(2)
+        n = b.info()["steps_done"]
+        for r in (0, 15, 16, 31, 32, 47, 48, 63):
+            lat = _single(ps[r], n)
+            _same_replica(b, r, lat, n)
+            lat.close()
+        p = ps[3]
+        o = O.Chain(O.make_params(p.Lx, p.Ly, T=p.T, J=p.J, D=p.D, seed=p.seed))
+        o.sweep(n)
+        assert np.array_equal(b.spins(3), o.spins())

@@ -195,6 +195,28 @@ def test_full_size_first_sweep_L2304():
     _same_energy(og["e_switched"], oo["e_switched"], g.N)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("T", [0.4, 0.8])
+def test_fp32_guarded_L1024(T):
+    """The precision workload's size: L = 1024, FP32-guarded against FP64 on the same seed
+    (identical decisions, energy within 1e-6 relative) and both against the oracle."""
+    L, n = 1024, 3
+    g64 = sco.Lattice(sco.make_params(L, T=T, seed=1))
+    g32 = sco.Lattice(sco.make_params(L, T=T, seed=1, precision=sco.FP32_GUARDED))
+    o = O.Chain(O.make_params(L, T=T, seed=1))
+    g64.sweep(n)
+    g32.sweep(n)
+    o.sweep(n)
+    s = o.spins()
+    assert np.array_equal(g64.spins(), s)
+    assert np.array_equal(g32.spins(), s)
+    assert np.array_equal(g32.accepts(), o.accepts())
+    e32, e64, eo = g32.observables(), g64.observables(), o.observables()
+    assert abs(e32["e_switched"] - e64["e_switched"]) <= 1e-6 * abs(e64["e_switched"])
+    _same_energy(e64["e_switched"], eo["e_switched"], g64.N)
+    assert e32["kw_rounds"] == eo["kw_rounds"] and e32["n_colours"] == eo["n_colours"]
+
+
 def test_library_expm1_within_its_bound():
     """The FP64 decisions take expm1 from the library's own branch-free implementation with a
     stated relative error bound of 2^-42 (carried in their error bounds); check it against
