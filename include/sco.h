@@ -195,11 +195,13 @@ typedef struct {
                                   and reduced largest colour first (order of Sec. 2.3.2 (2));
                                   1: one kernel per level, each vertex recolours as soon as
                                   its larger neighbours are done (2)'.  Same colours. */
-  int32_t kw_low;              /* first KW levels, while a group has at most 4096 vertices
+  int32_t kw_low;              /* first KW levels, while a group has at most kw_low_group vertices
                                   and g <= 64: 1: one block per group, internal edges staged
                                   in shared memory (rows when they do not fit); 2: one block
                                   per group, rows read at every level; 0: by the level
                                   kernels above.  Same colours and rounds. */
+  int32_t kw_low_group;        /* group-size cap of those levels: 1024, 2048 or 4096 vertices
+                                  (smaller: one level fewer, more blocks per SM) */
 } sco_batch_tuning;
 
 /* Creates a batch of n_replicas lattices from p[0 .. n_replicas-1] (1 <= n_replicas <= 1024,

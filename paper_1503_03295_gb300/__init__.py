@@ -35,7 +35,8 @@ class Params(C.Structure):
 class BatchTuning(C.Structure):
     _fields_ = [("steps_per_graph", C.c_int32), ("sweep_blocks_per_sm", C.c_int32),
                 ("kw_blocks_per_sm", C.c_int32), ("use_graph", C.c_int32),
-                ("kw_schedule", C.c_int32), ("kw_low", C.c_int32)]
+                ("kw_schedule", C.c_int32), ("kw_low", C.c_int32),
+                ("kw_low_group", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -345,9 +346,9 @@ class Batch:
         return t.as_dict()
 
     def set_tuning(self, steps_per_graph=4, sweep_blocks_per_sm=1, kw_blocks_per_sm=1,
-                   use_graph=1, kw_schedule=0, kw_low=1):
+                   use_graph=1, kw_schedule=0, kw_low=1, kw_low_group=2048):
         t = BatchTuning(steps_per_graph, sweep_blocks_per_sm, kw_blocks_per_sm, use_graph,
-                        kw_schedule, kw_low)
+                        kw_schedule, kw_low, kw_low_group)
         _check(load().sco_batch_set_tuning(self._h, C.byref(t)), "sco_batch_set_tuning")
 
     def tuning(self):

@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(256) kb_kw_init(const BatchDev B) {
 // One KW level for every replica.  The right-half slots of all replicas at level p are
 // numbered consecutively (a block-local scan of the per-replica counts); thread t owns
 // slots t + k * nthreads and recolours their vertices as in the single-lattice kernel.
-__global__ void __launch_bounds__(256, 4) kb_kw_level(const BatchDev B, unsigned p, int low_on) {
+__global__ void __launch_bounds__(256, 4) kb_kw_level(const BatchDev B, unsigned p,
+                                                    uint32_t low_gmax) {
   if (block_halted(B)) return;
   extern __shared__ uint32_t ksm[];
   const int R = B.R;
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(256, 4) kb_kw_level(const BatchDev B, unsigned
     const RepPlan pl = B.plan[r];
     const uint32_t b0 = B.site_start[r], N = B.site_start[r + 1] - b0;
     uint32_t n = 0;
-    if (p <= pl.levels && !(low_on && p <= kw_low_levels(pl.g, pl.levels))) {
+    if (p <= pl.levels && p > kw_low_levels(pl.g, pl.levels, low_gmax)) {
       const unsigned long long gsz = (unsigned long long)pl.g << p;
       n = (uint32_t)(((unsigned long long)N + gsz - 1) / gsz * ((unsigned long long)pl.g << (p - 1)));
     }
@@ -597,7 +598,7 @@ int batch_kw_occupancy(int schedule, int R, unsigned pal) {
   return n;
 }
 
-cudaError_t batch_low_setup(int R, int* blocks_per_sm, uint32_t* ecap) {
+cudaError_t batch_low_setup(int R, uint32_t gcap, int* blocks_per_sm, uint32_t* ecap) {
   int dev = 0, smem_sm = 0, smem_blk = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess)
@@ -611,12 +612,12 @@ cudaError_t batch_low_setup(int R, int* blocks_per_sm, uint32_t* ecap) {
     e = cudaFuncSetAttribute(k_kw_low, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  if (kw_low_smem(R, kLowMaxGroup, 0) > (size_t)(smem_blk - 64)) return cudaErrorInvalidValue;
+  if (kw_low_smem(R, gcap, 0) > (size_t)(smem_blk - 64)) return cudaErrorInvalidValue;
   int blocks = 1;
-  kw_low_shape(R, kLowMaxGroup, (size_t)smem_sm, (size_t)(smem_blk - 64), &blocks, ecap);
+  kw_low_shape(R, gcap, (size_t)smem_sm, (size_t)(smem_blk - 64), &blocks, ecap);
   int occ = 0;  // what is resident in fact
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_kw_low, kLowThreads,
-                                                    kw_low_smem(R, kLowMaxGroup, *ecap));
+                                                    kw_low_smem(R, gcap, *ecap));
   if (e != cudaSuccess) return e;
   *blocks_per_sm = occ < 1 ? 1 : (occ < blocks ? occ : blocks);
   return cudaSuccess;
@@ -664,8 +665,8 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
     return e;
   kb_kw_init<<<B.nblocks, kBatchBlock, 0, st>>>(B);
   ++*L.launches;
-  const int low_on = L.kw_low != 0;
-  if (low_on) {
+  const uint32_t low_gmax = L.kw_low != 0 ? L.low_gmax : 0u;
+  if (low_gmax) {
     KwLowView W{};
     W.R = B.R;
     W.site_start = B.site_start;
@@ -676,9 +677,10 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
     W.col8 = B.col8;
     W.cnt = B.cnt;
     W.halt = &B.ctl->flag;
-    W.gcap = kLowMaxGroup;
+    W.gmax = low_gmax;
+    W.gcap = low_gmax;
     W.ecap = L.low_ecap;
-    k_kw_low<<<(unsigned)L.low_grid, kLowThreads, kw_low_smem(B.R, kLowMaxGroup, L.low_ecap),
+    k_kw_low<<<(unsigned)L.low_grid, kLowThreads, kw_low_smem(B.R, low_gmax, L.low_ecap),
                st>>>(W);
     ++*L.launches;
   }
@@ -707,7 +709,7 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
     V.imeta = B.imeta;
     V.ilist = B.ilist;
     V.gmax = &B.ctl->gmax;
-    V.low_on = low_on;
+    V.low_gmax = low_gmax;
     if ((e = launch_coop(k_kw_bcr, (unsigned)L.kw_grid, 256, kw_bcr_smem(B.R, B.pal_cap), st,
                          V)) != cudaSuccess)
       return e;
@@ -715,7 +717,7 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
   } else {
     for (unsigned p = 1; p <= L.levels; ++p) {
       if ((e = launch_coop(kb_kw_level, (unsigned)L.kw_grid, 256, kw_smem(B.R), st, B, p,
-                           low_on)) != cudaSuccess)
+                           low_gmax)) != cudaSuccess)
         return e;
       ++*L.launches;
     }

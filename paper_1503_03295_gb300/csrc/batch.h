@@ -115,6 +115,7 @@ DevParams make_dev_params(const sco_params& p);
 struct BatchLaunch {
   int kw_schedule;  // 0: all levels in one kernel, buckets by colour; 1: one async kernel per level
   int kw_low;       // 0: no block-local levels; 1: staged edges; 2: rows at every level
+  uint32_t low_gmax;  // group-size cap of the block-local levels
   int low_grid;     // blocks of the block-local level kernel
   uint32_t low_ecap;  // its staged-edge capacity per group
   int kw_grid;     // blocks of the persistent KW kernel(s)
@@ -131,7 +132,7 @@ cudaError_t batch_step_end(const BatchDev& B, const BatchLaunch& L, cudaStream_t
 int batch_kw_occupancy(int schedule, int R, unsigned pal);
 // blocks per SM of the block-local level kernel and its staged-edge capacity (sets the
 // kernel's shared-memory limit)
-cudaError_t batch_low_setup(int R, int* blocks_per_sm, uint32_t* ecap);
+cudaError_t batch_low_setup(int R, uint32_t gcap, int* blocks_per_sm, uint32_t* ecap);
 int batch_sweep_occupancy(int precision, int R);
 size_t batch_sweep_smem(int R);
 

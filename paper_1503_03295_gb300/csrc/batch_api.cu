@@ -142,6 +142,12 @@ void set_grids(sco_batch* b) {
   const int sms = num_sms();
   b->L.kw_schedule = b->tune.kw_schedule;
   b->L.kw_low = b->tune.kw_low;
+  b->L.low_gmax = (uint32_t)b->tune.kw_low_group;
+  if (batch_low_setup(b->R, b->L.low_gmax, &b->low_occ, &b->low_ecap) != cudaSuccess) {
+    b->L.kw_low = 0;  // no block-local levels at this size (the level kernels take them)
+    b->low_occ = 1;
+    b->low_ecap = 0;
+  }
   b->L.low_grid = b->low_occ * sms;
   b->L.low_ecap = b->tune.kw_low == 2 ? 0u : b->low_ecap;
   b->kw_occ = batch_kw_occupancy(b->tune.kw_schedule, b->R, b->B.pal_cap);
@@ -278,7 +284,8 @@ bool valid_tuning(const sco_batch_tuning* t) {
   return t && t->steps_per_graph >= 1 && t->steps_per_graph <= 1024 &&
          t->sweep_blocks_per_sm >= 1 && t->kw_blocks_per_sm >= 1 &&
          (t->use_graph == 0 || t->use_graph == 1) && (t->kw_schedule == 0 || t->kw_schedule == 1) &&
-         t->kw_low >= 0 && t->kw_low <= 2;
+         t->kw_low >= 0 && t->kw_low <= 2 &&
+         (t->kw_low_group == 1024 || t->kw_low_group == 2048 || t->kw_low_group == 4096);
 }
 
 bool same_model(const sco_params& a, const sco_params& b) {
@@ -440,8 +447,7 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   if (e != cudaSuccess) return fail(from_cuda(e));
   b->tune.kw_schedule = 0;
   b->tune.kw_low = 1;
-  if ((e = batch_low_setup(n, &b->low_occ, &b->low_ecap)) != cudaSuccess)
-    return fail(from_cuda(e));
+  b->tune.kw_low_group = 2048;
   b->kw_occ = batch_kw_occupancy(0, n, B.pal_cap);
   b->sweep_occ = batch_sweep_occupancy(B.precision, n);
   b->tune.steps_per_graph = 4;
@@ -470,7 +476,8 @@ sco_status sco_batch_set_tuning(sco_batch* b, const sco_batch_tuning* t) {
   SCO_TRY(cudaStreamSynchronize(b->st));
   const bool grids = t->sweep_blocks_per_sm != b->tune.sweep_blocks_per_sm ||
                      t->kw_blocks_per_sm != b->tune.kw_blocks_per_sm ||
-                     t->kw_schedule != b->tune.kw_schedule || t->kw_low != b->tune.kw_low;
+                     t->kw_schedule != b->tune.kw_schedule || t->kw_low != b->tune.kw_low ||
+                     t->kw_low_group != b->tune.kw_low_group;
   b->tune = *t;
   b->tune.sweep_blocks_per_sm = std::min(t->sweep_blocks_per_sm, b->sweep_occ);
   if (grids) drop_graphs(b);
@@ -540,12 +547,18 @@ sco_status sco_batch_autotune(sco_batch* b, int32_t trial, sco_batch_tuning* cho
   }
   {
     std::vector<sco_batch_tuning> c;
-    for (int v : {0, 1})
-      if (v != best.kw_low) {
+    for (int v : {1024, 2048, 4096})
+      if (v != best.kw_low_group || best.kw_low != 1) {
         sco_batch_tuning t = best;
-        t.kw_low = v;
+        t.kw_low = 1;
+        t.kw_low_group = v;
         c.push_back(t);
       }
+    if (best.kw_low != 0) {
+      sco_batch_tuning t = best;
+      t.kw_low = 0;
+      c.push_back(t);
+    }
     try_dim(c);
   }
   {

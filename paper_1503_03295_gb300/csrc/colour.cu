@@ -335,7 +335,7 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   k_kw_meta<<<1, 1, 0, st>>>((uint32_t)N, g, M, magic, site_start, plan);
   ++*launches;
   // levels 1..low: one block per group of g 2^low vertices
-  const unsigned low = kw_low_levels(g, M);
+  const unsigned low = kw_low_levels(g, M, kLowMaxGroup);
   if (low > 0) {
     const uint32_t gcap = g << low;
     int lbps = 1;
@@ -353,6 +353,7 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     W.col8 = b.col8;
     W.cnt = cnt;
     W.halt = nullptr;
+    W.gmax = kLowMaxGroup;
     W.gcap = gcap;
     W.ecap = ecap;
     k_kw_low<<<(unsigned)grid, kLowThreads, kw_low_smem(1, gcap, ecap), st>>>(W);
@@ -399,7 +400,7 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     V.imeta = b.imeta;
     V.ilist = b.ilist;
     V.gmax = nullptr;
-    V.low_on = 1;
+    V.low_gmax = kLowMaxGroup;
     void* args[] = {(void*)&V};
     e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr, dim3((unsigned)(bps * num_sms())),
                                     dim3(256), args, sh, st);

@@ -49,7 +49,7 @@ struct KwView {
   uint32_t* imeta;
   uint32_t* ilist;
   const unsigned* gmax;         // optional: largest palette on the device (else pal)
-  int low_on;                   // levels 1..kw_low_levels(g, M) already done block-locally
+  uint32_t low_gmax;            // levels 1..kw_low_levels(g, M, low_gmax) done block-locally
 };
 
 constexpr int kItemList = kKwItemList;
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
       const RepPlan pl = V.plan[r];
       const uint32_t N = sbase[r + 1] - sbase[r];
       uint32_t n = 0;
-      if (p <= pl.levels && !(V.low_on && p <= kw_low_levels(pl.g, pl.levels))) {
+      if (p <= pl.levels && p > kw_low_levels(pl.g, pl.levels, V.low_gmax)) {
         const unsigned long long gsz = (unsigned long long)pl.g << p;
         n = (uint32_t)(((unsigned long long)N + gsz - 1) / gsz *
                        ((unsigned long long)pl.g << (p - 1)));

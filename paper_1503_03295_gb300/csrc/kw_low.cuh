@@ -28,11 +28,13 @@ constexpr uint32_t kLowMaxGroup = 4096;  // vertices of one block-local group
 constexpr uint32_t kLowMaxPal = 64;      // palettes g <= 64: colour sets are 64-bit masks
 constexpr int kLowThreads = 256;
 
-// Levels taken block-locally for a lattice of palette g and M levels (0: none).
-__host__ __device__ __forceinline__ unsigned kw_low_levels(uint32_t g, unsigned M) {
-  if (g == 0 || g > kLowMaxPal) return 0;
+// Levels taken block-locally for a lattice of palette g and M levels with groups of at most
+// gmax <= kLowMaxGroup vertices (0: none; gmax = 0 turns the block-local levels off).
+__host__ __device__ __forceinline__ unsigned kw_low_levels(uint32_t g, unsigned M,
+                                                          uint32_t gmax) {
+  if (g == 0 || g > kLowMaxPal || gmax > kLowMaxGroup) return 0;
   unsigned p = 0;
-  while (p < M && ((unsigned long long)g << (p + 1)) <= kLowMaxGroup) ++p;
+  while (p < M && ((unsigned long long)g << (p + 1)) <= gmax) ++p;
   return p;
 }
 
@@ -46,7 +48,8 @@ struct KwLowView {
   uint8_t* col8;                // colour (low byte), global vertex index
   DevCounters* cnt;             // R: lev_rounds
   const int* halt;              // optional: nonzero on entry -> return at once
-  uint32_t gcap;                // >= every group size g 2^p0, <= kLowMaxGroup, even
+  uint32_t gmax;                // group-size cap of kw_low_levels
+  uint32_t gcap;                // >= every group size g 2^p0, <= gmax, even
   uint32_t ecap;                // internal edges staged per group (0: rows at every level)
 };
 
@@ -136,10 +139,10 @@ __device__ __forceinline__ void low_for_nbrs(bool staged, uint32_t v, uint32_t b
   }
 }
 
-// Levels 1..kw_low_levels(g, M) of every lattice, one level-p0 group per block at a time.
+// Levels 1..kw_low_levels(g, M, gmax) of every lattice, one level-p0 group per block at a time.
 // Overwrites the words of those lattices (after the initial colours were written) and raises
 // lev_rounds[1..p0].
-__global__ void __launch_bounds__(kLowThreads) k_kw_low(const KwLowView V) {
+__global__ void __launch_bounds__(kLowThreads, 4) k_kw_low(const KwLowView V) {
   __shared__ int s_halt;
   if (threadIdx.x == 0) s_halt = V.halt ? ld_status(V.halt) : 0;
   __syncthreads();
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(kLowThreads) k_kw_low(const KwLowView V) {
   for (int r = tid; r < R; r += T) {
     const RepPlan pl = V.plan[r];
     const uint32_t b0 = V.site_start[r], N = V.site_start[r + 1] - b0;
-    const unsigned low = kw_low_levels(pl.g, pl.levels);
+    const unsigned low = kw_low_levels(pl.g, pl.levels, V.gmax);
     const uint32_t G = pl.g << low;
     sbase[r] = b0;
     gp[r] = low ? (N + G - 1) / G : 0u;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kLowThreads) k_kw_low(const KwLowView V) {
   auto group_of = [&](uint32_t gi, int& r, uint32_t& v0, uint32_t& n) {
     r = find_le(gp, R, gi);
     const RepPlan pl = V.plan[r];
-    const uint32_t G = pl.g << kw_low_levels(pl.g, pl.levels);
+    const uint32_t G = pl.g << kw_low_levels(pl.g, pl.levels, V.gmax);
     const uint32_t N = sbase[r + 1] - sbase[r];
     v0 = (gi - gp[r]) * G;
     n = min(G, N - v0);
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(kLowThreads) k_kw_low(const KwLowView V) {
     const RepPlan pl = V.plan[r];
     const uint32_t g = pl.g;
     const uint32_t m32 = low_magic(g);
-    const unsigned low = kw_low_levels(g, pl.levels);
+    const unsigned low = kw_low_levels(g, pl.levels, V.gmax);
     const uint32_t base = sbase[r];
     const uint32_t* rowp = V.row_ptr + base + v0;
     if (tid < 32) rl[tid] = 0;
@@ -332,13 +335,23 @@ __global__ void __launch_bounds__(kLowThreads) k_kw_low(const KwLowView V) {
                        ys[1] | (ys[2] << 16));
       }
       __syncthreads();
-      // buckets from the largest previous colour down, one vertex per thread
+      // buckets from the largest previous colour down, one vertex per thread; a thread's record
+      // of the next bucket (and that bucket's bounds) are loaded before this bucket's barrier
       uint32_t rmax = 0;
+      uint32_t s0 = bst[g - 1], s1 = bst[g];
+      uint4 qn = make_uint4(0, 0, 0, 0);
+      if (tid < s1 - s0) qn = rec[s0 + tid];
       for (int c = (int)g - 1; c >= 0; --c) {
-        const uint32_t s0 = bst[c], nb = bst[c + 1] - s0;
+        const uint32_t b0 = s0, nb = s1 - s0;
+        const uint4 q0 = qn;
+        if (c > 0) {
+          s1 = s0;
+          s0 = bst[c - 1];
+          if (tid < s1 - s0) qn = rec[s0 + tid];
+        }
         if (nb == 0) continue;
         for (uint32_t j = tid; j < nb; j += T) {
-          const uint4 q = rec[s0 + j];
+          const uint4 q = j == tid ? q0 : rec[b0 + j];
           const uint32_t v = q.z & kLowY, nn = (q.z >> 12) & 7u;
           unsigned long long mask = q.x | ((unsigned long long)q.y << 32);
           uint32_t rv = 0;

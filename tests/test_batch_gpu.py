@@ -93,7 +93,11 @@ def test_results_do_not_depend_on_tuning():
               dict(steps_per_graph=2, sweep_blocks_per_sm=4, kw_blocks_per_sm=2, use_graph=1,
                    kw_schedule=1),
               dict(steps_per_graph=2, sweep_blocks_per_sm=2, kw_blocks_per_sm=1, use_graph=1,
-                   kw_schedule=1, kw_low=2)):
+                   kw_schedule=1, kw_low=2),
+              dict(steps_per_graph=2, sweep_blocks_per_sm=2, kw_blocks_per_sm=2, use_graph=1,
+                   kw_low_group=4096),
+              dict(steps_per_graph=1, sweep_blocks_per_sm=2, kw_blocks_per_sm=2, use_graph=0,
+                   kw_schedule=1, kw_low_group=1024)):
         with sco.Batch(ps) as b:
             b.set_tuning(**t)
             b.run(4)
