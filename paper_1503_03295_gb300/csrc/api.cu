@@ -98,7 +98,7 @@ struct sco_ctx {
   int64_t launches = 0;
   Table tab;
   double* s = nullptr;
-  float* s32 = nullptr;
+  float4* s32 = nullptr;  // FP32 copy of the spins, one (x, y, z, 0) per site
   double* s_epoch = nullptr;
   SwitchBufs sw{};
   uint32_t* row_ptr = nullptr;
@@ -192,7 +192,7 @@ cudaError_t grow(T*& ptr, uint64_t& cap, uint64_t need) {
   return e;
 }
 
-sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float* src32) {
+sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4* src32) {
   PhaseTimer tm(c, kPhSwitch);
   // per-switch counters: n_half, n_dip, ovf_n, nnz and max_degree, max_degree_dip
   SCO_TRY(cudaMemsetAsync(c->cnt, 0, 4 * sizeof(unsigned long long), c->st));
@@ -358,7 +358,7 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   cudaError_t e = table_build(P, c->tab, c->st, &c->launches);
   if (e != cudaSuccess) return fail(from_cuda(e));
   e = cudaMalloc(&c->s, 3 * N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->s32, 3 * N * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->s32, N * sizeof(float4));
   if (e == cudaSuccess && p->n_sw > 1) e = cudaMalloc(&c->s_epoch, 3 * N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->sw.hslot, N * kSlotCap * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->sw.hcnt, N * sizeof(uint32_t));
@@ -614,8 +614,8 @@ sco_status sco_set_state(sco_ctx* c, const void* buf, size_t len) {
     if (!c->s_epoch) return SCO_ESTATE;
     SCO_TRY(cudaMemcpyAsync(c->s_epoch, body + 3 * N * sizeof(double), 3 * N * sizeof(double),
                             cudaMemcpyHostToDevice, c->st));
-    float* tmp32 = nullptr;
-    SCO_TRY(cudaMalloc(&tmp32, 3 * N * sizeof(float)));
+    float4* tmp32 = nullptr;
+    SCO_TRY(cudaMalloc(&tmp32, N * sizeof(float4)));
     cudaError_t e = spins_to_f32(N, c->s_epoch, tmp32, c->st, &c->launches);
     sco_status st = e == cudaSuccess
                         ? do_switch(c, (uint32_t)(c->t / c->p.n_sw), c->s_epoch, tmp32)

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 4 : 2) kb_switch(const BatchD
                       &B.ctl->ovf_n, &B.ctl->ovf_full, gs};
     const size_t so = 3 * (size_t)base;
     const uint32_t n_out =
-        switch_site<PREC>(sP, T, Wtot, d->sw64, d->xyq, d->xy32, B.s + so, B.s32 + so, epoch,
+        switch_site<PREC>(sP, T, Wtot, d->sw64, d->xyq, d->xy32, B.s + so, B.s32 + base, epoch,
                           d->mnn0, d->mnn1, i, o, n_dip, ghits, g32);
     B.hcnt[gs] = n_out;
     n_half = n_out;
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) kb_sweep(const BatchDe
       const DevParams& P = d->P;
       const size_t so = 3 * (size_t)base;
       double* s = B.s + so;
-      float* s32 = B.s32 + so;
+      float4* s32 = B.s32 + base;
       SiteCtx x;
       load_site(P, x, gs - base, s);
       if (!take_proposal(x, B.prop + base)) {
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) kb_sweep(const BatchDe
       const DevParams& P = d->P;
       const size_t so = 3 * (size_t)base;
       double* s = B.s + so;
-      float* s32 = B.s32 + so;
+      float4* s32 = B.s32 + base;
       SiteCtx x;
       load_site(P, x, gs - base, s);
       take_proposal(x, B.prop + base);

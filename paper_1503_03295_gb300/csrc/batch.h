@@ -74,7 +74,7 @@ struct BatchDev {
   int precision;
   int n_sw;
   double* s;
-  float* s32;
+  float4* s32;  // FP32 copy of the spins, one (x, y, z, 0) per site
   uint8_t* acc;
   uint32_t* hslot;
   uint32_t* hcnt;

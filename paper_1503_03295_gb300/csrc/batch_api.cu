@@ -401,7 +401,7 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   A(&B.cnt, n * sizeof(DevCounters));
   A(&B.ctl, sizeof(BatchCtl));
   A(&B.s, 3 * N * sizeof(double));
-  A(&B.s32, 3 * N * sizeof(float));
+  A(&B.s32, N * sizeof(float4));
   A(&B.acc, N);
   A(&B.hslot, N * kSlotCap * sizeof(uint32_t));
   A(&B.hcnt, N * sizeof(uint32_t));
@@ -441,7 +441,7 @@ sco_status sco_batch_init(const sco_params* p, int32_t n, void* stream, sco_batc
   if (e == cudaSuccess) e = cudaMemsetAsync(B.acc, 0, N, b->st);
   for (int r = 0; r < n && e == cudaSuccess; ++r) {
     const size_t so = 3 * (size_t)b->site_start[r];
-    e = spins_init(b->P[r], B.s + so, B.s32 + so, b->st, &b->launches);
+    e = spins_init(b->P[r], B.s + so, B.s32 + b->site_start[r], b->st, &b->launches);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) return fail(from_cuda(e));
@@ -643,7 +643,8 @@ sco_status sco_batch_set_spins(sco_batch* b, int32_t r, const double* xyz, int32
   const size_t N = (size_t)b->P[r].N, so = 3 * (size_t)b->site_start[r];
   SCO_TRY(cudaMemcpyAsync(b->B.s + so, xyz, 3 * N * sizeof(double),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->st));
-  SCO_TRY(spins_to_f32((int64_t)N, b->B.s + so, b->B.s32 + so, b->st, &b->launches));
+  SCO_TRY(spins_to_f32((int64_t)N, b->B.s + so, b->B.s32 + b->site_start[r], b->st,
+                       &b->launches));
   SCO_TRY(cudaStreamSynchronize(b->st));
   return SCO_OK;
 }

@@ -59,9 +59,9 @@ void table_free(Table& t);
 void table_free_xy(Table& t);
 
 // ---- init / observables (spins.cu) ----
-cudaError_t spins_init(const DevParams& P, double* s, float* s32, cudaStream_t st,
+cudaError_t spins_init(const DevParams& P, double* s, float4* s32, cudaStream_t st,
                        int64_t* launches);
-cudaError_t spins_to_f32(int64_t N, const double* s, float* s32, cudaStream_t st,
+cudaError_t spins_to_f32(int64_t N, const double* s, float4* s32, cudaStream_t st,
                          int64_t* launches);
 cudaError_t observables_run(const DevParams& P, const double* s, const uint32_t* row_ptr,
                             const uint32_t* col, const double2* xy, bool have_graph,
@@ -80,7 +80,7 @@ struct SwitchBufs {
   uint32_t ovf_cap;
   uint64_t* scan_tmp;
 };
-cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float* s32,
+cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float4* s32,
                        int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,
                        cudaStream_t st, int64_t* launches);
 cudaError_t csr_scan(const DevParams& P, SwitchBufs& b, uint32_t* row_ptr, DevCounters* cnt,
@@ -117,7 +117,7 @@ cudaError_t bucket_run(const DevParams& P, uint32_t g, const uint32_t* row_ptr, 
                        DevCounters* cnt, cudaStream_t st, int64_t* launches);
 
 // ---- sweep.cu ----
-cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float* s32,
+cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,
                       const uint32_t* off, uint32_t g, uint64_t step, int precision,
                       uint8_t* acc, uint32_t* defer, uint32_t* dcnt, double4_32a* prop,

@@ -10,7 +10,7 @@ namespace {
 
 // Uniform initial spins: Philox tag INIT, counter (i, 0, a), Marsaglia attempt a = 0..63;
 // (0, 0, 1) if all 64 attempts fail (probability ~1e-43).
-__global__ void k_init(DevParams P, double* __restrict__ s, float* __restrict__ s32) {
+__global__ void k_init(DevParams P, double* __restrict__ s, float4* __restrict__ s32) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= P.N) return;
   double x = 0.0, y = 0.0, z = 1.0;
@@ -22,16 +22,12 @@ __global__ void k_init(DevParams P, double* __restrict__ s, float* __restrict__ 
   s[i] = x;
   s[P.N + i] = y;
   s[2 * P.N + i] = z;
-  if (s32) {
-    s32[i] = (float)x;
-    s32[P.N + i] = (float)y;
-    s32[2 * P.N + i] = (float)z;
-  }
+  if (s32) s32[i] = make_float4((float)x, (float)y, (float)z, 0.f);
 }
 
-__global__ void k_to_f32(int64_t n, const double* __restrict__ s, float* __restrict__ s32) {
+__global__ void k_to_f32(int64_t n, const double* __restrict__ s, float4* __restrict__ s32) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) s32[i] = (float)s[i];
+  if (i < n) s32[i] = make_float4((float)s[i], (float)s[n + i], (float)s[2 * n + i], 0.f);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -159,16 +155,16 @@ __global__ void __launch_bounds__(256) k_full_energy(DevParams P, const double* 
 
 }  // namespace
 
-cudaError_t spins_init(const DevParams& P, double* s, float* s32, cudaStream_t st,
+cudaError_t spins_init(const DevParams& P, double* s, float4* s32, cudaStream_t st,
                        int64_t* launches) {
   k_init<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P, s, s32);
   ++*launches;
   return cudaGetLastError();
 }
 
-cudaError_t spins_to_f32(int64_t N, const double* s, float* s32, cudaStream_t st,
+cudaError_t spins_to_f32(int64_t N, const double* s, float4* s32, cudaStream_t st,
                          int64_t* launches) {
-  k_to_f32<<<(unsigned)((3 * N + 255) / 256), 256, 0, st>>>(3 * N, s, s32);
+  k_to_f32<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, s, s32);
   ++*launches;
   return cudaGetLastError();
 }

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) k_propose(const DevParams P, uint64_t ste
 template <int PREC>
 __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) k_sweep(const DevParams P, const Sw64* __restrict__ sw,
                                                const float4* __restrict__ sw32,
-                                               double* __restrict__ s, float* __restrict__ s32,
+                                               double* __restrict__ s, float4* __restrict__ s32,
                                                const uint32_t* __restrict__ row_ptr,
                                                const uint32_t* __restrict__ col,
                                                const uint32_t* __restrict__ perm,
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128, PREC == 1 ? 6 : 5) k_sweep(const DevParam
 
 // Settles the deferred sites of a colour: one warp per site, FP64 then double-double.
 __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* __restrict__ sw,
-                                                 double* __restrict__ s, float* __restrict__ s32,
+                                                 double* __restrict__ s, float4* __restrict__ s32,
                                                  const uint32_t* __restrict__ row_ptr,
                                                  const uint32_t* __restrict__ col,
                                                  const uint32_t* __restrict__ off,
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
 
 }  // namespace
 
-cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float* s32,
+cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,
                       const uint32_t* off, uint32_t g, uint64_t step, int precision,
                       uint8_t* acc, uint32_t* defer, uint32_t* dcnt, double4_32a* prop,

@@ -128,7 +128,7 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
 // eps_r = 2^-23, and a compensated (Neumaier) sum of the V' - V terms.
 __device__ __forceinline__ int accept_fp32(const DevParams& P, const SiteCtx& c,
                                            const float4* __restrict__ sw,
-                                           const float* __restrict__ s32,
+                                           const float4* __restrict__ s32,
                                            const uint32_t* __restrict__ row_ptr,
                                            const uint32_t* __restrict__ col) {
   if (c.u < 0x1p-100) return 2;
@@ -147,7 +147,8 @@ __device__ __forceinline__ int accept_fp32(const DevParams& P, const SiteCtx& c,
     const int32_t dy = (int32_t)yj - c.yi;
     const float4 t =
         __ldg(&sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)]);
-    const float bx = s32[j], by = s32[P.N + j], bz = s32[2 * P.N + j];
+    const float4 sj = s32[j];
+    const float bx = sj.x, by = sj.y, bz = sj.z;
     const float fx = (float)dx, fy = (float)dy;
     const float tp = t.y * (bx * fx + by * fy);
     const float gx = t.x * bx - tp * fx;
@@ -184,9 +185,10 @@ __device__ __forceinline__ int accept_fp32(const DevParams& P, const SiteCtx& c,
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (nb[q] < 0) continue;
-      h0 += s32[nb[q]];
-      h1 += s32[P.N + nb[q]];
-      h2 += s32[2 * P.N + nb[q]];
+      const float4 sq = s32[nb[q]];
+      h0 += sq.x;
+      h1 += sq.y;
+      h2 += sq.z;
     }
     const float bj = P.bJ_f;
     tex = -bj * ((nx - ax) * h0 + (ny - ay) * h1 + (nz - az) * h2);
@@ -242,17 +244,13 @@ __device__ __forceinline__ void load_site(const DevParams& P, SiteCtx& c, uint32
 }
 
 __device__ __forceinline__ void write_site(const DevParams& P, const SiteCtx& c, bool ok,
-                                           double* __restrict__ s, float* __restrict__ s32,
+                                           double* __restrict__ s, float4* __restrict__ s32,
                                            uint8_t* __restrict__ acc) {
   if (ok) {
     s[c.i] = c.Sn[0];
     s[P.N + c.i] = c.Sn[1];
     s[2 * P.N + c.i] = c.Sn[2];
-    if (s32) {
-      s32[c.i] = (float)c.Sn[0];
-      s32[P.N + c.i] = (float)c.Sn[1];
-      s32[2 * P.N + c.i] = (float)c.Sn[2];
-    }
+    if (s32) s32[c.i] = make_float4((float)c.Sn[0], (float)c.Sn[1], (float)c.Sn[2], 0.f);
   }
   acc[c.i] = ok ? 1 : 0;
 }

@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 4 : 2) k_switch(const DevPara
                                                 const double* __restrict__ xyq,
                                                 const float4* __restrict__ xy32,
                                                 const double* __restrict__ s,
-                                                const float* __restrict__ s32, uint32_t epoch,
+                                                const float4* __restrict__ s32, uint32_t epoch,
                                                 int32_t mnn0, int32_t mnn1, SwitchBufs b,
                                                 DevCounters* __restrict__ cnt) {
   __shared__ uint64_t sW[kNear];
@@ -109,7 +109,7 @@ __global__ void k_rowsort(int64_t N, const uint32_t* __restrict__ row_ptr,
 
 }  // namespace
 
-cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float* s32,
+cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float4* s32,
                        int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,
                        cudaStream_t st, int64_t* launches) {
   cudaError_t e = cudaMemsetAsync(b.indeg, 0, P.N * sizeof(uint32_t), st);

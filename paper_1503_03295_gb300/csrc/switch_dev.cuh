@@ -251,7 +251,7 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
                                                 const double* __restrict__ xyq,
                                                 const float4* __restrict__ xy32,
                                                 const double* __restrict__ s,
-                                                const float* __restrict__ s32, uint32_t epoch,
+                                                const float4* __restrict__ s32, uint32_t epoch,
                                                 int32_t mnn0, int32_t mnn1, uint32_t i,
                                                 const SwitchOut& o, unsigned long long& n_dip,
                                                 unsigned& ghits, unsigned& g32) {
@@ -260,9 +260,10 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
   const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
   float Si32[3] = {0.f, 0.f, 0.f};
   if (PREC == 1) {
-    Si32[0] = s32[i];
-    Si32[1] = s32[P.N + i];
-    Si32[2] = s32[2 * P.N + i];
+    const float4 si = s32[i];
+    Si32[0] = si.x;
+    Si32[1] = si.y;
+    Si32[2] = si.z;
   }
   uint32_t n_out = 0;
   bool nn0 = false, nn1 = false;
@@ -302,7 +303,8 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
       const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
       bool surv;
       if (PREC == 1) {
-        const float Sj32[3] = {s32[j], s32[P.N + j], s32[2 * P.N + j]};
+        const float4 sj = s32[j];
+        const float Sj32[3] = {sj.x, sj.y, sj.z};
         surv = survives_fp32(P, __ldg(&xy32[tix]), sw, __ldg(&xyq[tix]), Si32, Sj32, Si, Sj, dx,
                              dy, A, wU, g32, ghits);
       } else {
