@@ -260,6 +260,16 @@ sco_status sco_selftest_expm1(int64_t n, uint64_t seed, double* max_rel_err,
 sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t degree, double* max_rel_err,
                                   double* max_rel_diff_cuda);
 
+/* Device self-test of the library's own natural logarithm for 0 < x <= 1, used by the FP64
+ * candidate search of the switch (table-driven reduction, degree-4 polynomial; stated relative
+ * error bound 2^-49, carried in that search's margin).  Evaluates it at n >= 17 points (16 fixed
+ * ones, then Philox-drawn values over all octaves of (2^-53, 1) and just below 1, from `seed`)
+ * and returns the largest relative error against the library's double-double log
+ * (max_rel_err; at x = 1 the absolute value, 0 expected) and against CUDA's log
+ * (max_rel_diff_cuda, may be NULL).  Synchronous; uses the current device. */
+sco_status sco_selftest_log(int64_t n, uint64_t seed, double* max_rel_err,
+                            double* max_rel_diff_cuda);
+
 /* Waits for the context's stream; returns the sticky device status. */
 sco_status sco_sync(sco_ctx* c);
 

@@ -109,6 +109,8 @@ def load():
         "sco_batch_sync": ([vp], st),
         "sco_selftest_expm1_deg": ([C.c_int64, C.c_uint64, C.c_int32, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)], st),
+        "sco_selftest_log": ([C.c_int64, C.c_uint64, C.POINTER(C.c_double),
+                              C.POINTER(C.c_double)], st),
         "sco_selftest_expm1": ([C.c_int64, C.c_uint64, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)], st),
     }
@@ -153,6 +155,14 @@ def selftest_expm1(n=1 << 24, seed=1, degree=8):
     a, b = C.c_double(), C.c_double()
     _check(load().sco_selftest_expm1_deg(int(n), int(seed), int(degree), C.byref(a), C.byref(b)),
            "sco_selftest_expm1_deg")
+    return a.value, b.value
+
+
+def selftest_log(n=1 << 24, seed=1):
+    """Largest relative error of the library's log (0 < x <= 1) against double-double and
+    against CUDA's log (see sco_selftest_log)."""
+    a, b = C.c_double(), C.c_double()
+    _check(load().sco_selftest_log(int(n), int(seed), C.byref(a), C.byref(b)), "sco_selftest_log")
     return a.value, b.value
 
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "expm1_poly.h"
+#include "log_table.h"
 
 namespace sco {
 
@@ -161,6 +162,34 @@ __device__ __forceinline__ double expm1_np_deg(double x) {
   return (xb < 0 && (xb & 0x7FFFFFFFFFFFFFFFll) > 0x4044000000000000ll) ? -1.0 : res;
 }
 __device__ __forceinline__ double expm1_np(double x) { return expm1_np_deg<8>(x); }
+
+// The library's own natural logarithm for normal 0 < x <= 1 (table-driven after Tang, ACM TOMS
+// 16(4), 1990; table and coefficients in log_table.h): x = 2^k m, m in [sqrt(2)/2, sqrt(2)), F =
+// 1 + j/256 nearest to m (j and F from the bits), r = (m - F) / F with |r| < 0.0028 (m - F
+// exact), log x = k ln2 + log F + log1p(r), log1p(r) = r + r^2 q(r), q of degree 4 (truncation
+// below 2^-53.5 |r|).  Relative error below 2^-50: r off by 2^-52 relative, the polynomial by a
+// few ulp of r, the sums by an ulp of |k ln2 + log F| <= 3.6 |log x| (the worst case k = 0,
+// F != 1, where |log F| >= 0.0039 > |r|).  Stated as kLogRelErr = 2^-49.  13 FP64 operations.
+constexpr double kLogRelErr = 0x1p-49;
+__device__ __forceinline__ double log_np(double x) {
+  const long long xb = __double_as_longlong(x);
+  int k = (int)((xb >> 52) & 0x7FF) - 1023;
+  const long long frac = xb & 0xFFFFFFFFFFFFFll;
+  const bool big = frac >= 0x6A09E667F3BCDll;  // m = 1.frac >= sqrt(2): halve it
+  k += big ? 1 : 0;
+  const double m = __longlong_as_double(frac | (big ? 0x3FE0000000000000ll : 0x3FF0000000000000ll));
+  // j = round((m - 1) 256): for m in [1, 2) round(frac 2^-44); for m/2 round(frac 2^-45) - 128
+  const int j = big ? (int)(((frac >> 44) + 1) >> 1) - 128 : (int)(((frac >> 43) + 1) >> 1);
+  const long long fb = j >= 0 ? (0x3FF0000000000000ll | ((long long)j << 44))
+                              : (0x3FE0000000000000ll | ((long long)(128 + j) << 45));
+  const double* t = kLogTab[j - kLogJmin];
+  const double inv = __ldg(t), lh = __ldg(t + 1), ll = __ldg(t + 2);
+  const double r = (m - __longlong_as_double(fb)) * inv;
+  const double q = fma(fma(fma(fma(kLogC6, r, kLogC5), r, kLogC4), r, kLogC3), r, kLogC2);
+  const double lp = fma(r * r, q, r);
+  const double kd = (double)k;
+  return fma(kd, kLogLn2Hi, lh) + (lp + fma(kd, kLogLn2Lo, ll));
+}
 __device__ __forceinline__ double expm1_np6(double x) { return expm1_np_deg<6>(x); }
 
 // Sweep constants of a pair at (|dx|, |dy|) for the FP64 decisions (64 bytes).  With the

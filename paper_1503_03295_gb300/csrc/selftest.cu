@@ -1,7 +1,7 @@
-// selftest.cu -- device self-test of the library's own elementary function expm1 (the degree-8
-// expm1_np of the FP64 switch, the degree-6 expm1_np6 of the FP64 sweep decisions): its relative
-// error against the double-double expm1 and its difference from the CUDA expm1, on points
-// spread over [-50, 0.35].
+// selftest.cu -- device self-test of the library's own elementary functions, expm1 (the degree-8
+// expm1_np of the FP64 switch, the degree-6 expm1_np6 of the FP64 sweep decisions) on points of
+// [-50, 0.35] and log_np (the FP64 candidate search of the switch) on points of (0, 1]: relative
+// error against the double-double versions and difference from CUDA's.
 #include <cstdint>
 #include <cstring>
 
@@ -45,20 +45,43 @@ __global__ void k_expm1_test(int64_t n, uint64_t seed, dd ln2, unsigned long lon
   atomic_max_pos(&out[1], e_lib);
 }
 
-}  // namespace
-}  // namespace sco
+// The library's log on n points of (0, 1] (16 fixed ones: 1 and its neighbours, the sqrt(2)/2
+// switch, table boundaries, powers of two; then alternately 2^-e (1 + f) and 1 - 2^-e (1 + f) / 2
+// with e in [1, 53] and f in [0, 1) from Philox: all octaves, and values just below 1), against
+// the double-double log and CUDA's log.
+__global__ void k_log_test(int64_t n, uint64_t seed, dd ln2, unsigned long long* out) {
+  const double fixed[16] = {1.0, 0x1.fffffffffffffp-1, 0x1.ffffffffffffep-1, 0x1p-53,
+                            0.5, 0x1.6a09e667f3bcdp-1, 0x1.6a09e667f3bccp-1, 0x1.6a09e667f3bcep-1,
+                            0x1.ff8p-1, 0x1.ff7ffffffffffp-1, 0x1.008p0 * 0.5, 0.75,
+                            0x1.0000000000001p-1, 0x1p-20, 0.999, 1e-10};
+  double e_dd = 0.0, e_lib = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double x;
+    if (k < 16) {
+      x = fixed[k];
+    } else {
+      const W4 w = philox((uint64_t)k, 0, 0, 9, seed, 0);
+      const int e = 1 + (int)(w.w[0] % 53);
+      const double f = u53(w.w[1]);
+      x = (k & 1) ? 1.0 - ldexp(0.5 + 0.5 * f, -e) : ldexp(1.0 + f * (1.0 - 0x1p-53), -e);
+    }
+    const double y = log_np(x);
+    if (x == 1.0) {
+      e_dd = fmax(e_dd, fabs(y));  // exact 0 expected
+      continue;
+    }
+    const dd r = dd_log(dd_from(x), ln2);
+    const dd d = dd_sub(dd_from(y), r);
+    e_dd = fmax(e_dd, fabs(d.hi / r.hi));
+    const double yl = log(x);
+    e_lib = fmax(e_lib, fabs((y - yl) / yl));
+  }
+  atomic_max_pos(&out[0], e_dd);
+  atomic_max_pos(&out[1], e_lib);
+}
 
-using namespace sco;
-
-extern "C" sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t degree,
-                                             double* max_rel_err, double* max_rel_diff_cuda) {
-  if (n < 17 || !max_rel_err || (degree != 6 && degree != 8)) return SCO_EINVAL;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SCO_ECUDA;
-  unsigned long long* d = nullptr;
-  if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return SCO_ENOMEM;
-  cudaError_t e = cudaMemset(d, 0, 2 * sizeof(unsigned long long));
-  // ln 2 = 2 atanh(1/3) in double-double
+dd ln2_dd() {  // ln 2 = 2 atanh(1/3) in double-double
   const dd third = dd_div(dd_from(1.0), dd_from(3.0));
   const dd x2 = dd_mul(third, third);
   dd pw = third, sum = dd_from(0.0);
@@ -66,10 +89,21 @@ extern "C" sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t d
     sum = dd_add(sum, dd_div(pw, dd_from(2.0 * k + 1.0)));
     pw = dd_mul(pw, x2);
   }
-  const dd ln2 = dd_ldexp(sum, 1);
+  return dd_ldexp(sum, 1);
+}
+
+// Runs test kernel `which` (0: expm1 degree 8, 1: expm1 degree 6, 2: log) on n points.
+sco_status run_test(int which, int64_t n, uint64_t seed, double* err, double* diff) {
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SCO_ECUDA;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return SCO_ENOMEM;
+  cudaError_t e = cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+  const dd ln2 = ln2_dd();
   if (e == cudaSuccess) {
-    if (degree == 8) k_expm1_test<8><<<1024, 256>>>(n, seed, ln2, d);
-    else k_expm1_test<6><<<1024, 256>>>(n, seed, ln2, d);
+    if (which == 0) k_expm1_test<8><<<1024, 256>>>(n, seed, ln2, d);
+    else if (which == 1) k_expm1_test<6><<<1024, 256>>>(n, seed, ln2, d);
+    else k_log_test<<<1024, 256>>>(n, seed, ln2, d);
     e = cudaGetLastError();
   }
   unsigned long long h[2] = {0, 0};
@@ -79,9 +113,26 @@ extern "C" sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t d
   double a, b;
   std::memcpy(&a, &h[0], 8);
   std::memcpy(&b, &h[1], 8);
-  *max_rel_err = a;
-  if (max_rel_diff_cuda) *max_rel_diff_cuda = b;
+  *err = a;
+  if (diff) *diff = b;
   return SCO_OK;
+}
+
+}  // namespace
+}  // namespace sco
+
+using namespace sco;
+
+extern "C" sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t degree,
+                                             double* max_rel_err, double* max_rel_diff_cuda) {
+  if (n < 17 || !max_rel_err || (degree != 6 && degree != 8)) return SCO_EINVAL;
+  return run_test(degree == 8 ? 0 : 1, n, seed, max_rel_err, max_rel_diff_cuda);
+}
+
+extern "C" sco_status sco_selftest_log(int64_t n, uint64_t seed, double* max_rel_err,
+                                       double* max_rel_diff_cuda) {
+  if (n < 17 || !max_rel_err) return SCO_EINVAL;
+  return run_test(2, n, seed, max_rel_err, max_rel_diff_cuda);
 }
 
 extern "C" sco_status sco_selftest_expm1(int64_t n, uint64_t seed, double* max_rel_err,

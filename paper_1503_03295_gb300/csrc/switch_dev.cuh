@@ -99,15 +99,16 @@ __device__ __forceinline__ uint64_t ceil_u64(float x) {
   return q + ((q << (-ex)) != mant ? 1ull : 0ull);
 }
 
-// tau = -ln(u+) / (beta D 2^-58) carries < 2^-49 relative error (log, fl(beta D), fl(2^58 / bD),
-// one product); the candidate is certain when W_k - W_s >= tau (1 + 2^-46) and
+// tau = -ln(u+) / (beta D 2^-58) carries < 2^-48 relative error (log_np within kLogRelErr =
+// 2^-49, fl(beta D), fl(2^58 / bD), one product); the candidate is certain when
+// W_k - W_s >= tau (1 + 2^-46) and
 // W_(k-1) - W_s < tau (1 - 2^-46), compared as integers (ceil of the bounds).
 __device__ __forceinline__ int64_t next_candidate(const DevParams& P, const NearTable& T,
                                                   int64_t s, uint64_t Ws, uint64_t Wtot,
                                                   uint64_t wE, unsigned& ghits) {
   if (s >= T.K - 1 || !P.switching) return T.K;
   const double up = u53pos(wE);
-  const double tau = -log(up) * P.inv_bD58;
+  const double tau = -log_np(up) * P.inv_bD58;
   const uint64_t rem = Wtot - Ws;
   const uint64_t thr = ceil_u64d(tau);
   int64_t k = T.K;

@@ -229,3 +229,13 @@ def test_library_expm1_within_its_bound():
     err, diff = sco.selftest_expm1(1 << 24, seed=4, degree=6)
     assert err < 2.0 ** -31
     assert diff < 2.0 ** -31
+
+
+def test_library_log_within_its_bound():
+    """The FP64 candidate search of the switch takes log from the library's own table-driven
+    implementation with a stated relative error bound of 2^-49 (carried in its margin); check it
+    against double-double on 16M points of (0, 1] (all octaves, values just below 1, the
+    reduction and table boundaries)."""
+    err, diff = sco.selftest_log(1 << 24, seed=5)
+    assert err < 2.0 ** -49
+    assert diff < 2.0 ** -49
