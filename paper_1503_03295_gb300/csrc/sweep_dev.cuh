@@ -48,9 +48,9 @@ constexpr int kScale32 = 60;
 //   operations; it must stay below 2^-10 or the decision is left undecided.
 
 // FP64 decision (0: reject, 1: accept, 2: undecided).  eps_r = 2^-52 (unit roundoff, with
-// margin), eps_f = 2^-50 for the CUDA logarithms (within 4 ulp), eps_z = kExpm1RelErr6 for the
-// library's expm1_np6 (two per pair, doubled: 4 eps_z).  Compares, minima and renormalisation
-// tests work on the bits of positive doubles (integer pipe).
+// margin), eps_f = kLogRelErr for the library's log_np (inputs in (0, 1]), eps_z =
+// kExpm1RelErr6 for the library's expm1_np6 (two per pair, doubled: 4 eps_z).  Compares, minima
+// and renormalisation tests work on the bits of positive doubles (integer pipe).
 __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
                                            const Sw64* __restrict__ sw,
                                            const double* __restrict__ s,
@@ -110,13 +110,13 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     tex = -(P.beta * P.J) * dot;
     bex = 0x1p-44 * fabs(P.beta * P.J);
   }
-  const double lo = log(pz_o), ln = log(pz_n);
+  const double lo = log_np(pz_o), ln = log_np(pz_n);
   // prod z = stored product * 2^(-kScale * count)
   const double scale = (double)((sc_n - sc_o) * kScale64) * P.ln2_hi;
-  const double lu = log(c.u);
+  const double lu = log_np(c.u);
   const double mu = lu + ((bdv + tex) + ((lo - ln) + scale));
   const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
-                          0x1p-50 * (fabs(lo) + fabs(ln) + fabs(lu)) + bex +
+                          kLogRelErr * (fabs(lo) + fabs(ln) + fabs(lu)) + bex +
                           0x1p-51 * (fabs(scale) + fabs(tex) + fabs(bdv) + fabs(mu)));
   if (mu < -B) return 1;
   if (mu > B) return 0;
@@ -322,8 +322,8 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
     ++n;
   }
   // per lane: log of its products, with the renormalisation folded in
-  const double lo = log(pz_o) - (double)(sc_o * kScale64) * P.ln2_hi;
-  const double ln = log(pz_n) - (double)(sc_n * kScale64) * P.ln2_hi;
+  const double lo = log_np(pz_o) - (double)(sc_o * kScale64) * P.ln2_hi;
+  const double ln = log_np(pz_n) - (double)(sc_n * kScale64) * P.ln2_hi;
   const double lsum = warp_sum_d(lo - ln);
   const double labs = warp_sum_d(fabs(lo) + fabs(ln));
   bdv = warp_sum_d(bdv);
@@ -350,10 +350,10 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
     tex = -(P.beta * P.J) * dot;
     bex = 0x1p-44 * fabs(P.beta * P.J);
   }
-  const double lu = log(c.u);
+  const double lu = log_np(c.u);
   const double mu = lu + ((bdv + tex) + lsum);
   const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
-                          0x1p-50 * (labs + fabs(lu)) + 0x1p-49 * labs + bex +
+                          kLogRelErr * (labs + fabs(lu)) + 0x1p-49 * labs + bex +
                           0x1p-51 * (fabs(tex) + fabs(bdv) + fabs(mu)));
   if (mu < -B) return 1;
   if (mu > B) return 0;
