@@ -93,7 +93,10 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     ++n;
   }
   if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;  // n <= 2^(32 - clz n)
-  const double lin = n > 0 ? ldexp((double)n, dmax + 2) : 0.0;
+  // n 2^(dmax + 2), the power of two from its bits (dmax + 2 <= -10 here; below -1022: 0)
+  const double lin = n > 0 && dmax + 2 >= -1022
+                         ? (double)n * __longlong_as_double((long long)(dmax + 2 + 1023) << 52)
+                         : 0.0;
   double tex = 0.0, bex = 0.0;
   if (P.J != 0.0) {
     double h0 = 0.0, h1 = 0.0, h2 = 0.0;
@@ -333,7 +336,10 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (bad) return 2;
   if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;
-  const double lin = n > 0 ? ldexp((double)n, dmax + 2) : 0.0;
+  // n 2^(dmax + 2), the power of two from its bits (dmax + 2 <= -10 here; below -1022: 0)
+  const double lin = n > 0 && dmax + 2 >= -1022
+                         ? (double)n * __longlong_as_double((long long)(dmax + 2 + 1023) << 52)
+                         : 0.0;
   double tex = 0.0, bex = 0.0;
   if (P.J != 0.0) {
     double h0 = 0.0, h1 = 0.0, h2 = 0.0;
