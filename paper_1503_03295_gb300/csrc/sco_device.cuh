@@ -217,6 +217,12 @@ __device__ __forceinline__ bool neg_strict(double x) {
 __device__ __forceinline__ unsigned long long pos_bits(double x) {
   return (unsigned long long)__double_as_longlong(x);
 }
+// a signed integer ordered like the value of a (non-NaN) double: ord(a) < ord(b) iff a < b
+// (the two zeros map to 0 and -1; no FP64 instruction)
+__device__ __forceinline__ long long ord_bits(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b) - 1;
+}
 // biased exponent field of a double >= 0 (x >= 2^(e - 1023) for normal x; 0 for zero and
 // subnormals, which then read as tiny)
 __device__ __forceinline__ int exp_field(double x) {

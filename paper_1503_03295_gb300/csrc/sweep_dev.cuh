@@ -58,7 +58,8 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
                                            const uint32_t* __restrict__ col) {
   const double S0 = c.S[0], S1 = c.S[1], S2 = c.S[2];
   const double N0 = c.Sn[0], N1 = c.Sn[1], N2 = c.Sn[2];
-  double bdv = 0.0, pz_o = 1.0, pz_n = 1.0, c0s = 0.0;
+  double bdv = 0.0, pz_o = 1.0, pz_n = 1.0;
+  unsigned long long c0m = 0;  // bits of the largest c0 (n max c0 bounds their sum)
   int dmax = -2046;  // largest e(c0_j) - e(z_j)
   const unsigned long long small_b = pos_bits(0x1p-600);
   int sc_o = 0, sc_n = 0, n = 0;
@@ -89,7 +90,7 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     if (pos_bits(pz_o) < small_b) { pz_o *= 0x1p600; ++sc_o; }
     bdv += xn - xo;
     dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
-    c0s += t.c0;
+    c0m = max(c0m, pos_bits(t.c0));
     ++n;
   }
   if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;  // n <= 2^(32 - clz n)
@@ -118,6 +119,7 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
   const double scale = (double)((sc_n - sc_o) * kScale64) * P.ln2_hi;
   const double lu = log_np(c.u);
   const double mu = lu + ((bdv + tex) + ((lo - ln) + scale));
+  const double c0s = (double)n * __longlong_as_double((long long)c0m);
   const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
                           kLogRelErr * (fabs(lo) + fabs(ln) + fabs(lu)) + bex +
                           0x1p-51 * (fabs(scale) + fabs(tex) + fabs(bdv) + fabs(mu)));

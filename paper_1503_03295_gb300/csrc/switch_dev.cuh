@@ -113,9 +113,12 @@ __device__ __forceinline__ int64_t next_candidate(const DevParams& P, const Near
   const uint64_t thr = ceil_u64d(tau);
   int64_t k = T.K;
   if (thr <= rem) k = T.lower_bound(s + 1, Ws + thr);
-  const double eps = 0x1p-46;
-  const uint64_t hi = ceil_u64d(tau * (1.0 + eps));  // W_k - W_s >= hi: surely a candidate
-  const uint64_t lo = ceil_u64d(tau * (1.0 - eps));  // W_k-1 - W_s < lo: surely not
+  // thr = ceil(tau): ceil(tau (1 + 2^-46)) <= thr + floor(thr 2^-46) + 1 = hi and
+  // tau (1 - 2^-46) >= (thr - 1)(1 - 2^-46) >= thr - floor(thr 2^-46) - 2 = lo (saturating),
+  // in integers: no FP64 instruction
+  const uint64_t m46 = thr >> 46;
+  const uint64_t hi = thr + m46 + 1 < thr ? ~0ull : thr + m46 + 1;  // >= hi: surely a candidate
+  const uint64_t lo = thr > m46 + 2 ? thr - m46 - 2 : 0ull;         // < lo: surely not
   bool certain = true;
   if (k < T.K && T.w(k) - Ws < hi) certain = false;
   if (k - 1 > s && T.w(k - 1) - Ws >= lo) certain = false;
@@ -192,8 +195,10 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t,
   const double b = (t.a1 * ss - pa * pb) - t.bvm;
   const double pr = -expm1_np(b);
   const double mu = pr - u1 * q;
-  if (mu > t.bsw) return true;
-  if (mu < -t.bsw) return false;
+  // mu > bsw, mu < -bsw on ordered bit images (bsw > 0: ord(-bsw) = -ord(bsw) - 1)
+  const long long om = ord_bits(mu), ob = ord_bits(t.bsw);
+  if (om > ob) return true;
+  if (om < -ob - 1) return false;
   ++ghits;
   return survives_dd(P, Si, Sj, dx, dy, A, u1);
 }
