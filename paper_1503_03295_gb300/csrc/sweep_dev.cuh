@@ -80,8 +80,9 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     const double gx = a1 * bx - tp * fx;
     const double gy = a1 * by - tp * fy;
     const double gz = a1 * bz;
-    const double xn = (N0 * gx + N1 * gy + N2 * gz) - bvm;
-    const double xo = (S0 * gx + S1 * gy + S2 * gz) - bvm;
+    // three FMAs each; c0 covers the roundings (those touching bvm stay below 2^-51 bvm)
+    const double xn = fma(N0, gx, fma(N1, gy, fma(N2, gz, -bvm)));
+    const double xo = fma(S0, gx, fma(S1, gy, fma(S2, gz, -bvm)));
     if (!neg_strict(xn) || !neg_strict(xo)) return 2;
     const double zn = -expm1_np6(xn), zo = -expm1_np6(xo);
     pz_n *= zn;
@@ -310,8 +311,8 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
     const double gx = t.a1 * bx - tp * fx;
     const double gy = t.a1 * by - tp * fy;
     const double gz = t.a1 * bz;
-    const double xn = (c.Sn[0] * gx + c.Sn[1] * gy + c.Sn[2] * gz) - t.bvm;
-    const double xo = (c.S[0] * gx + c.S[1] * gy + c.S[2] * gz) - t.bvm;
+    const double xn = fma(c.Sn[0], gx, fma(c.Sn[1], gy, fma(c.Sn[2], gz, -t.bvm)));
+    const double xo = fma(c.S[0], gx, fma(c.S[1], gy, fma(c.S[2], gz, -t.bvm)));
     if (!neg_strict(xn) || !neg_strict(xo)) {
       bad = 1;
       continue;

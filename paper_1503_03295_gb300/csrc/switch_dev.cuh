@@ -192,7 +192,7 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t,
   const double ss = Si[0] * Sj[0] + Si[1] * Sj[1] + Si[2] * Sj[2];
   const double pa = Si[0] * ax3 + Si[1] * ay3;
   const double pb = Sj[0] * fx + Sj[1] * fy;
-  const double b = (t.a1 * ss - pa * pb) - t.bvm;
+  const double b = fma(t.a1, ss, fma(-pa, pb, -t.bvm));  // c0 covers these two roundings
   const double pr = -expm1_np(b);
   const double mu = pr - u1 * q;
   // mu > bsw, mu < -bsw on ordered bit images (bsw > 0: ord(-bsw) = -ord(bsw) - 1)
