@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) k_propose(const DevParams P, uint64_t ste
 // appended to the deferred list of the colour and settled by k_resolve (one warp per site),
 // so that no thread of this kernel runs the long FP64 / double-double evaluations.
 template <int PREC>
-__global__ void __launch_bounds__(128, PREC == 1 ? 6 : 8) k_sweep(const DevParams P, const Sw64* __restrict__ sw,
+__global__ void __launch_bounds__(128, 8) k_sweep(const DevParams P, const Sw64* __restrict__ sw,
                                                const float4* __restrict__ sw32,
                                                double* __restrict__ s, float4* __restrict__ s32,
                                                const uint32_t* __restrict__ row_ptr,
