@@ -367,6 +367,46 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
     };
     int c = next_bucket((int)pal);
     if (fast) {
+      // one item: record-driven, or from its row when the record overflowed
+      auto recolour = [&](KwItem& it, int cb) -> bool {
+        const int r = find_le(sbase, R, it.gv);
+        unsigned rm = 0;
+        bool mine;
+        if (it.meta & kItemSlow) {  // more larger neighbours than the record holds
+          const uint32_t base = sbase[r];
+          KwRow w;
+          kw_fetch(w, it.gv, V.row_ptr, V.col);
+          mine = kw_recolour(it.gv - base, (uint32_t)cb, w, p, V.plan[r].g, V.plan[r].magic,
+                             V.col, V.word + base, V.col8 + base, rm, V.status, t_start,
+                             V.ns_limit);
+        } else {
+          mine = kw_item_recolour(it, V, p, rm, t_start);
+        }
+        atomicMax(&smax[r], rm);
+        return mine;
+      };
+      // the largest colours' buckets hold at most one block's worth of vertices each: block 0
+      // takes that run alone, one __syncthreads apart, and one grid barrier publishes it
+      int ct = (int)pal;
+      while (ct > 0 && start[ct] - start[ct - 1] <= blockDim.x) --ct;
+      if (c >= ct) {  // a non-empty tail
+        if (blockIdx.x == 0) {
+          bool mine = true;
+          for (int cb = c; cb >= ct; --cb) {
+            const uint32_t b0 = start[cb], n = start[cb + 1] - b0;
+            if (n == 0) continue;
+            if (mine && threadIdx.x < n) {
+              KwItem it;
+              kw_item_fetch(it, V, b0 + threadIdx.x);
+              mine = recolour(it, cb);
+            }
+            __syncthreads();
+          }
+        }
+        // false for every block once an error was reported (status read after the barrier)
+        ok = grid_sync(V.bar, V.status, V.ns_limit);
+        c = next_bucket(ct);
+      }
       KwItem it;
       it.gv = kNone;
       if (c >= 0 && gtid < start[c + 1] - start[c]) kw_item_fetch(it, V, start[c] + gtid);
@@ -375,19 +415,7 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
         bool mine = true;
         for (uint32_t q = gtid; q < n && mine; q += nth) {
           if (q != gtid) kw_item_fetch(it, V, b0 + q);
-          const int r = find_le(sbase, R, it.gv);
-          unsigned rm = 0;
-          if (it.meta & kItemSlow) {  // more larger neighbours than the record holds
-            const uint32_t base = sbase[r];
-            KwRow w;
-            kw_fetch(w, it.gv, V.row_ptr, V.col);
-            mine = kw_recolour(it.gv - base, (uint32_t)c, w, p, V.plan[r].g, V.plan[r].magic,
-                               V.col, V.word + base, V.col8 + base, rm, V.status, t_start,
-                               V.ns_limit);
-          } else {
-            mine = kw_item_recolour(it, V, p, rm, t_start);
-          }
-          atomicMax(&smax[r], rm);
+          mine = recolour(it, c);
         }
         grid_arrive(V.bar, s_old);
         const int cn = next_bucket(c);
