@@ -10,7 +10,7 @@ namespace sco {
 namespace {
 
 template <int PREC>
-__global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_switch(const DevParams P, const uint64_t* __restrict__ W,
+__global__ void __launch_bounds__(256, 4) k_switch(const DevParams P, const uint64_t* __restrict__ W,
                                                 const uint32_t* __restrict__ disp,
                                                 const Sw64* __restrict__ sw64,
                                                 const double* __restrict__ xyq,
