@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) kb_clear(const BatchDev B) {
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) kb_switch(const BatchDev B) {
+__global__ void __launch_bounds__(256, 4) kb_switch(const BatchDev B) {
   if (block_halted(B)) return;
   __shared__ uint64_t sW[kNear];
   __shared__ uint32_t sD[kNear];
