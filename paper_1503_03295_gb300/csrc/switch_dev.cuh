@@ -151,13 +151,16 @@ __device__ __forceinline__ int64_t next_candidate_fp32(const DevParams& P, const
     E = -logf(u);
   }
   const float tau = E * P.inv_bD58_f;
-  const float eps = 0x1p-18f;
   const uint64_t rem = Wtot - Ws;
   const uint64_t thr = ceil_u64(tau);
   int64_t k = T.K;
   if (thr <= rem) k = T.lower_bound(s + 1, Ws + thr);
-  const uint64_t hi = ceil_u64(tau * (1.0f + eps));  // W_k - W_s >= hi: surely a candidate
-  const uint64_t lo = ceil_u64(tau * (1.0f - eps));  // W_k-1 - W_s < lo: surely not
+  // margins 2^-18 around tau from thr = ceil(tau), in integers (conservative, as in the FP64
+  // search): ceil(tau (1 + 2^-18)) <= thr + floor(thr 2^-18) + 1 = hi, and
+  // tau (1 - 2^-18) >= thr - floor(thr 2^-18) - 2 = lo (saturating)
+  const uint64_t m18 = thr >> 18;
+  const uint64_t hi = thr + m18 + 1 < thr ? ~0ull : thr + m18 + 1;  // >= hi: surely a candidate
+  const uint64_t lo = thr > m18 + 2 ? thr - m18 - 2 : 0ull;         // < lo: surely not
   bool certain = tau < 0x1p62f;
   if (k < T.K && T.w(k) - Ws < hi) certain = false;
   if (k - 1 > s && T.w(k - 1) - Ws >= lo) certain = false;
