@@ -208,14 +208,14 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t,
 
 // FP32 screen of the same test (FP32-guarded form): spins from the FP32 shadow
 // (|dS| <= 2^-24 per component), table constants rounded to FP32, expm1f within 4 ulp.
-// Falls through to the FP64 test (and from there to double-double) inside the bound.
+// Falls through to the FP64 test (and from there to double-double) inside the bound; only
+// then are the FP64 spins of i and j read from the SoA array s.
 __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
                                               const Sw64* __restrict__ sw, double q64,
-                                              const float* Si32,
-                                              const float* Sj32, const double* Si,
-                                              const double* Sj, int32_t dx, int32_t dy,
-                                              uint64_t A, uint64_t wU, unsigned& g32,
-                                              unsigned& ghits) {
+                                              const float* Si32, const float* Sj32,
+                                              const double* __restrict__ s, int64_t i, int64_t j,
+                                              int32_t dx, int32_t dy, uint64_t A, uint64_t wU,
+                                              unsigned& g32, unsigned& ghits) {
   const float fr2 = (float)(dx * dx + dy * dy), fx = (float)dx, fy = (float)dy;
   // u truncated to 24 bits: 0 <= u - u24 < 2^-24, inside the 2^-19 q term of the bound
   const float u24 = __uint2float_rn((uint32_t)(wU >> 40)) * 0x1p-24f;
@@ -237,6 +237,8 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
   if (mu < -B) return false;
   ++g32;
   const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy);
+  const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
+  const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
   return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, A, u53(wU), ghits);
 }
 
@@ -266,9 +268,13 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
                                                 unsigned& ghits, unsigned& g32) {
   const int32_t yi = (int32_t)site_row(i, P);
   const int32_t xi = (int32_t)(i - (uint32_t)yi * (uint32_t)P.Lx);
-  const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
+  double Si[3] = {0.0, 0.0, 0.0};
   float Si32[3] = {0.f, 0.f, 0.f};
-  if (PREC == 1) {
+  if (PREC == 0) {
+    Si[0] = s[i];
+    Si[1] = s[P.N + i];
+    Si[2] = s[2 * P.N + i];
+  } else {
     const float4 si = s32[i];
     Si32[0] = si.x;
     Si32[1] = si.y;
@@ -309,14 +315,14 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
       const int64_t j = xj + (int64_t)P.Lx * yj;
       const uint64_t A = Wk - (k > 0 ? T.w(k - 1) : 0ull);
       const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
-      const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
       bool surv;
       if (PREC == 1) {
         const float4 sj = s32[j];
         const float Sj32[3] = {sj.x, sj.y, sj.z};
-        surv = survives_fp32(P, __ldg(&xy32[tix]), sw, __ldg(&xyq[tix]), Si32, Sj32, Si, Sj, dx,
-                             dy, A, wU, g32, ghits);
+        surv = survives_fp32(P, __ldg(&xy32[tix]), sw, __ldg(&xyq[tix]), Si32, Sj32, s,
+                             (int64_t)i, j, dx, dy, A, wU, g32, ghits);
       } else {
+        const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
         surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), Si, Sj, dx, dy, A, u53(wU), ghits);
       }
       if (surv) {
