@@ -111,11 +111,14 @@ cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32
   k_propose<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P, step, prop);
   ++*launches;
   const unsigned nres = (unsigned)(2 * num_sms());
-  // one launch per colour in ascending order; a class holds about N / g sites
+  // one launch per colour in ascending order; a class holds about N / g sites.  The grid is a
+  // whole number of blocks per SM (every SM gets the same share of a class: the FP64 form is
+  // bound by each SM's FP64 pipe) and at most the resident 8 per SM of __launch_bounds__.
   const int64_t per = P.N / (g > 0 ? g : 1) + 1;
+  const int64_t sms = num_sms();
   int64_t nb = (per + 127) / 128;
-  const int64_t cap = 16 * (int64_t)num_sms();
-  if (nb > cap) nb = cap;
+  nb = (nb + sms - 1) / sms * sms;
+  if (nb > 8 * sms) nb = 8 * sms;
   if (nb < 1) nb = 1;
   for (uint32_t c = 0; c < g; ++c) {
     if (precision == 1)

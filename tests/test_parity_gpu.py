@@ -178,7 +178,8 @@ def test_checkpoint_resume_bit_exact():
 
 @pytest.mark.slow
 def test_full_size_first_sweep_L2304():
-    """The workload size of the throughput benchmark: L = 2304, T = 0.6 D, seed 0."""
+    """The workload size of the throughput benchmark: L = 2304, T = 0.6 D, seed 0, in both
+    forms the benchmark times (FP64 and FP32-guarded), against one oracle MC step."""
     g, o = _pair(2304, T=0.6, seed=0)
     t = g.table()
     r = O.table(2304)
@@ -193,6 +194,16 @@ def test_full_size_first_sweep_L2304():
     og, oo = g.observables(), o.observables()
     assert og["kw_rounds"] == oo["kw_rounds"]
     _same_energy(og["e_switched"], oo["e_switched"], g.N)
+    g.close()
+    g32 = sco.Lattice(sco.make_params(2304, T=0.6, seed=0, precision=sco.FP32_GUARDED))
+    g32.sweep(1)
+    _same_graph(g32, o)
+    assert np.array_equal(g32.colours().astype(np.int32), o.colours())
+    assert np.array_equal(g32.spins(), o.spins())
+    assert np.array_equal(g32.accepts(), o.accepts())
+    o32 = g32.observables()
+    assert o32["kw_rounds"] == oo["kw_rounds"]
+    assert abs(o32["e_switched"] - og["e_switched"]) <= 1e-6 * abs(og["e_switched"])
 
 
 @pytest.mark.slow
