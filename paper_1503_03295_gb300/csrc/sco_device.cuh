@@ -94,19 +94,49 @@ __device__ __forceinline__ double scaled53(uint64_t m) {
 __device__ __forceinline__ double u53(uint64_t w) { return scaled53(w >> 11); }
 __device__ __forceinline__ double u53pos(uint64_t w) { return scaled53((w >> 11) + 1); }
 
+// 2 u - 1 for u = u53(w): with m = w >> 11, fl(fl(2u) - 1) is the exact (m - 2^52) 2^-52
+// (|m - 2^52| <= 2^52 needs no rounding; +0 when 2u = 1), built from its bits.
+__device__ __forceinline__ double centred53(uint64_t w) {
+  const long long d = (long long)(w >> 11) - (1ll << 52);
+  if (d == 0) return 0.0;
+  const uint64_t mag = (uint64_t)(d < 0 ? -d : d);  // <= 2^52
+  const int e = 63 - __clzll((long long)mag);
+  const uint64_t mant = (mag << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  const uint64_t b = ((uint64_t)(e - 52 + 1023) << 52) | mant;
+  return __longlong_as_double((long long)(d < 0 ? b | 0x8000000000000000ull : b));
+}
+
+// 2 v for a normal or zero v (exact: one more in the exponent field).
+__device__ __forceinline__ double twice(double v) {
+  const long long b = __double_as_longlong(v);
+  return (b & 0x7FFFFFFFFFFFFFFFll) == 0 ? v : __longlong_as_double(b + (1ll << 52));
+}
+
 // Marsaglia (1972): reject unless 0 < s = a1^2 + a2^2 < 1, then
-// S = (2 a1 sqrt(1-s), 2 a2 sqrt(1-s), 1 - 2s).  Each operation rounded on its own so that
-// the spin is the same bit pattern on every IEEE machine.
+// S = (2 a1 sqrt(1-s), 2 a2 sqrt(1-s), 1 - 2s), a = 2u - 1.  Each operation rounded on its own
+// so that the spin is the same bit pattern on every IEEE machine; the doublings are exact, so
+// fl(fl(2 a1) h) = 2 fl(a1 h) and fl(1 - fl(2 s)) = fma(-2, s, 1).  Split in two so that a loop
+// over attempts can take the square root once, after it.
+__device__ __forceinline__ bool marsaglia_point(uint64_t w0, uint64_t w1, double& a1, double& a2,
+                                                double& s) {
+  a1 = centred53(w0);
+  a2 = centred53(w1);
+  s = __dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2));
+  const unsigned long long sb = (unsigned long long)__double_as_longlong(s);  // s >= +0
+  return sb != 0ull && sb < 0x3FF0000000000000ull;
+}
+__device__ __forceinline__ void marsaglia_spin(double a1, double a2, double s, double& x,
+                                               double& y, double& z) {
+  const double h = __dsqrt_rn(__dsub_rn(1.0, s));
+  x = twice(__dmul_rn(a1, h));
+  y = twice(__dmul_rn(a2, h));
+  z = __fma_rn(-2.0, s, 1.0);
+}
 __device__ __forceinline__ bool marsaglia(uint64_t w0, uint64_t w1, double& x, double& y,
                                           double& z) {
-  const double a1 = __dsub_rn(__dmul_rn(2.0, u53(w0)), 1.0);
-  const double a2 = __dsub_rn(__dmul_rn(2.0, u53(w1)), 1.0);
-  const double s = __dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2));
-  if (s >= 1.0 || s == 0.0) return false;
-  const double h = __dsqrt_rn(__dsub_rn(1.0, s));
-  x = __dmul_rn(__dmul_rn(2.0, a1), h);
-  y = __dmul_rn(__dmul_rn(2.0, a2), h);
-  z = __dsub_rn(1.0, __dmul_rn(2.0, s));
+  double a1, a2, s;
+  if (!marsaglia_point(w0, w1, a1, a2, s)) return false;
+  marsaglia_spin(a1, a2, s, x, y, z);
   return true;
 }
 

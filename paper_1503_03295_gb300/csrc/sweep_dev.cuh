@@ -216,15 +216,21 @@ __device__ __forceinline__ int accept_fp32(const DevParams& P, const SiteCtx& c,
 
 // Proposal of site i at MC step t (Philox tag PROPOSE, counter (i, t, a)); false if all 64
 // attempts were rejected.
+// The square root and the spin are computed once, after the attempts (whose count differs
+// between the lanes of a warp).
 __device__ __forceinline__ bool propose(const DevParams& P, SiteCtx& c, uint64_t step) {
-  for (uint64_t a = 0; a < 64; ++a) {
+  double a1 = 0.0, a2 = 0.0, s = 0.0;
+  uint64_t wu = 0;
+  bool ok = false;
+  for (uint64_t a = 0; a < 64 && !ok; ++a) {
     const W4 w = philox((uint64_t)c.i, step, a, kTagPropose, P.key0, P.key1);
-    if (marsaglia(w.w[0], w.w[1], c.Sn[0], c.Sn[1], c.Sn[2])) {
-      c.u = u53(w.w[2]);
-      return true;
-    }
+    ok = marsaglia_point(w.w[0], w.w[1], a1, a2, s);
+    wu = w.w[2];
   }
-  return false;
+  if (!ok) return false;
+  marsaglia_spin(a1, a2, s, c.Sn[0], c.Sn[1], c.Sn[2]);
+  c.u = u53(wu);
+  return true;
 }
 
 // Proposals are drawn for every site of a lattice by k_propose before the colour classes of a
