@@ -93,12 +93,12 @@ __global__ void __launch_bounds__(256, 4) kb_switch(const BatchDev B) {
     const uint32_t gs = base + i;
     const uint64_t Wtot = K > 0 ? __ldg(&W[K - 1]) : 0;
     const uint32_t epoch = (uint32_t)(B.ctl->step / (unsigned long long)B.n_sw);
-    const SwitchOut o{B.hslot + (size_t)gs * kSlotCap, B.indeg + base, B.ovf, B.ovf_cap,
-                      &B.ctl->ovf_n, &B.ctl->ovf_full, gs};
+    const SwitchOut o{B.hslot, B.indeg + base, B.ovf, B.ovf_cap, &B.ctl->ovf_n,
+                      &B.ctl->ovf_full};
     const size_t so = 3 * (size_t)base;
     const uint32_t n_out =
         switch_site<PREC>(sP, T, Wtot, d->sw64, d->xyq, d->xy32, B.s + so, B.s32 + base, epoch,
-                          d->mnn0, d->mnn1, i, o, n_dip, ghits, g32);
+                          d->mnn0, d->mnn1, i, gs, o, n_dip, ghits, g32);
     B.hcnt[gs] = n_out;
     n_half = n_out;
   }

@@ -29,6 +29,7 @@ struct DevCounters {
   double acc[8];                    // observable accumulators
   unsigned int lev_rounds[32];      // deepest dependency chain per KW level
   unsigned int bar[2];              // grid barrier of the persistent colouring kernel
+  unsigned int sw_next;             // next unclaimed site of the persistent switch kernel
 };
 
 // ---- scan.cu ----

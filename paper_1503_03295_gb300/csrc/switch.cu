@@ -9,6 +9,9 @@ namespace sco {
 
 namespace {
 
+// Persistent: each warp claims 32 sites at a time from a global counter, and a lane whose walk
+// ends takes up the next claimed site at once, so that the lanes of a warp stay busy although
+// the number of candidates differs from site to site (Poisson, mean about 14 at T = 0.6D).
 template <int PREC>
 __global__ void __launch_bounds__(256, 4) k_switch(const DevParams P, const uint64_t* __restrict__ W,
                                                 const uint32_t* __restrict__ disp,
@@ -28,17 +31,48 @@ __global__ void __launch_bounds__(256, 4) k_switch(const DevParams P, const uint
   }
   __syncthreads();
   const NearTable T{sW, sD, W, disp, nnear, P.K};
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const uint64_t Wtot = P.K > 0 ? __ldg(&W[P.K - 1]) : 0;
+  const SwitchOut o{b.hslot, b.indeg, b.ovf, b.ovf_cap, &cnt->ovf_n, &cnt->ovf_full};
+  const uint32_t N = (uint32_t)P.N;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned below = (1u << lane) - 1u;
   unsigned long long n_half = 0, n_dip = 0;
   unsigned ghits = 0, g32 = 0;
-  if (i < P.N) {
-    const uint64_t Wtot = P.K > 0 ? __ldg(&W[P.K - 1]) : 0;
-    const SwitchOut o{b.hslot + i * (int64_t)kSlotCap, b.indeg, b.ovf, b.ovf_cap, &cnt->ovf_n,
-                      &cnt->ovf_full, (uint32_t)i};
-    const uint32_t n_out = switch_site<PREC>(P, T, Wtot, sw64, xyq, xy32, s, s32, epoch, mnn0,
-                                             mnn1, (uint32_t)i, o, n_dip, ghits, g32);
-    b.hcnt[i] = n_out;
-    n_half = n_out;
+  SiteWalk<PREC> a;
+  bool active = false, drained = false;  // drained, pool and pool_n are warp-uniform
+  uint32_t pool = 0, pool_n = 0;
+  for (;;) {
+    unsigned need = __ballot_sync(0xffffffffu, !active);
+    while (need != 0u && !drained) {
+      if (pool_n == 0u) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&cnt->sw_next, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= N) {
+          drained = true;
+          break;
+        }
+        pool = base;
+        pool_n = min(32u, N - base);
+      }
+      const uint32_t take = min((uint32_t)__popc(need), pool_n);
+      const uint32_t rank = (uint32_t)__popc(need & below);
+      if (!active && rank < take) {
+        walk_begin<PREC>(P, s, s32, pool + rank, pool + rank, a);
+        active = true;
+      }
+      pool += take;
+      pool_n -= take;
+      need = __ballot_sync(0xffffffffu, !active);
+    }
+    if (__ballot_sync(0xffffffffu, active) == 0u) break;
+    if (active && !walk_step<PREC>(P, T, Wtot, sw64, xyq, xy32, s, s32, epoch, mnn0, mnn1, o,
+                                   a, n_dip, ghits, g32)) {
+      const uint32_t n_out = walk_end<PREC>(P, mnn0, mnn1, o, a);
+      b.hcnt[a.i] = n_out;
+      n_half += n_out;
+      active = false;
+    }
   }
   n_half = warp_sum_u64(n_half);
   n_dip = warp_sum_u64(n_dip);
@@ -113,8 +147,21 @@ cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, cons
                        int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,
                        cudaStream_t st, int64_t* launches) {
   cudaError_t e = cudaMemsetAsync(b.indeg, 0, P.N * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&cnt->sw_next, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  const unsigned nb = (unsigned)((P.N + 255) / 256);
+  if (P.N <= 0) return cudaSuccess;
+  // persistent grid: the resident blocks, at most one thread per site
+  static int bps[2] = {0, 0};
+  const int pi = precision == 1 ? 1 : 0;
+  if (bps[pi] == 0) {
+    e = pi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[pi], k_switch<1>, 256, 0)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[pi], k_switch<0>, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (bps[pi] < 1) bps[pi] = 1;
+  }
+  int64_t nb64 = (int64_t)bps[pi] * num_sms();
+  if (nb64 > (P.N + 255) / 256) nb64 = (P.N + 255) / 256;
+  const unsigned nb = (unsigned)nb64;
   if (precision == 1)
     k_switch<1><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.sw64, t.xyq, t.xy32, s, s32, epoch,
                                      t.m_nn[0], t.m_nn[1], b, cnt);

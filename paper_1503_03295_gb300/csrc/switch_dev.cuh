@@ -242,20 +242,144 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
   return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, A, u53(wU), ghits);
 }
 
-// Where site i writes its upper neighbours: kSlotCap slots of its own, then an overflow list
-// shared by all sites (entry: site id, j | flag).  indeg counts lower neighbours per site.
+// Where a site writes its upper neighbours: kSlotCap slots of its own (row `id` of hslot), then
+// an overflow list shared by all sites (entry: site id, j | flag).  indeg counts lower
+// neighbours per (local) site.
 struct SwitchOut {
-  uint32_t* slot;
+  uint32_t* hslot;
   uint32_t* indeg;
   uint32_t* ovf;
   uint32_t ovf_cap;
   unsigned long long* ovf_n;
   int* status;
-  uint32_t site_id;  // id of site i in the overflow list
 };
 
-// Switches the half-plane pairs of site i (local index) at this epoch; returns the number of
-// upper neighbours written (dipolar survivors plus exchange-only bonds).
+// One site's walk along its half-plane list: the candidate search of Sec. 2.1 with the state it
+// carries from one candidate to the next, so that a thread can take the candidates one at a time
+// (and take up another site when its list ends).
+template <int PREC>
+struct SiteWalk {
+  uint32_t i;   // local site index (the Philox counter)
+  uint32_t id;  // site id in the slots and the overflow list
+  int32_t xi, yi;
+  double Si[3];    // FP64 form
+  float Si32[3];   // FP32-screened form
+  int64_t sidx;    // last candidate (-1 before the first)
+  uint64_t Ws;     // W at sidx
+  uint32_t n;      // candidates drawn; Philox block n / 2, words 0-1 or 2-3
+  W4 w;
+  uint32_t n_out;
+  bool nn0, nn1;
+};
+
+__device__ __forceinline__ void switch_emit(const SwitchOut& o, uint32_t id, uint32_t& n_out,
+                                            uint32_t jv) {
+  if (n_out < (uint32_t)kSlotCap) {
+    o.hslot[(size_t)id * kSlotCap + n_out] = jv;
+  } else {
+    const unsigned long long idx = atomicAdd(o.ovf_n, 1ull);
+    if (idx < o.ovf_cap) {
+      o.ovf[2 * idx] = id;
+      o.ovf[2 * idx + 1] = jv;
+    } else {
+      set_status(o.status, kStatusCapacity);
+    }
+  }
+  ++n_out;
+  atomicAdd(&o.indeg[jv & kIndexMask], 1u);
+}
+
+template <int PREC>
+__device__ __forceinline__ void walk_begin(const DevParams& P, const double* __restrict__ s,
+                                           const float4* __restrict__ s32, uint32_t i,
+                                           uint32_t id, SiteWalk<PREC>& a) {
+  a.i = i;
+  a.id = id;
+  a.yi = (int32_t)site_row(i, P);
+  a.xi = (int32_t)(i - (uint32_t)a.yi * (uint32_t)P.Lx);
+  if (PREC == 0) {
+    a.Si[0] = s[i];
+    a.Si[1] = s[P.N + i];
+    a.Si[2] = s[2 * P.N + i];
+  } else {
+    const float4 si = s32[i];
+    a.Si32[0] = si.x;
+    a.Si32[1] = si.y;
+    a.Si32[2] = si.z;
+  }
+  a.sidx = -1;
+  a.Ws = 0;
+  a.n = 0;
+  a.n_out = 0;
+  a.nn0 = false;
+  a.nn1 = false;
+}
+
+// Draws the next candidate of the walk and, if it lies on the lattice, tests its survival
+// (emitting the pair if it survives).  Returns false once the list is exhausted.
+template <int PREC>
+__device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T, uint64_t Wtot,
+                                          const Sw64* __restrict__ sw,
+                                          const double* __restrict__ xyq,
+                                          const float4* __restrict__ xy32,
+                                          const double* __restrict__ s,
+                                          const float4* __restrict__ s32, uint32_t epoch,
+                                          int32_t mnn0, int32_t mnn1, const SwitchOut& o,
+                                          SiteWalk<PREC>& a, unsigned long long& n_dip,
+                                          unsigned& ghits, unsigned& g32) {
+  if ((a.n & 1u) == 0u)
+    a.w = philox((uint64_t)a.i, epoch, (uint64_t)(a.n >> 1), kTagSwitch, P.key0, P.key1);
+  const uint64_t wE = (a.n & 1u) ? a.w.w[2] : a.w.w[0];
+  const uint64_t wU = (a.n & 1u) ? a.w.w[3] : a.w.w[1];
+  ++a.n;
+  const int64_t k = PREC == 1 ? next_candidate_fp32(P, T, a.sidx, a.Ws, Wtot, wE, g32, ghits)
+                              : next_candidate(P, T, a.sidx, a.Ws, Wtot, wE, ghits);
+  if (k >= P.K) return false;
+  const uint32_t d = T.d(k);
+  const int32_t dx = (int16_t)(d & 0xFFFFu), dy = (int32_t)(d >> 16);
+  const uint64_t Wk = T.w(k);
+  const int32_t xj = a.xi + dx, yj = a.yi + dy;
+  if (xj >= 0 && xj < P.Lx && yj < P.Ly) {
+    const int64_t j = xj + (int64_t)P.Lx * yj;
+    const uint64_t A = Wk - (k > 0 ? T.w(k - 1) : 0ull);
+    const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
+    bool surv;
+    if (PREC == 1) {
+      const float4 sj = s32[j];
+      const float Sj32[3] = {sj.x, sj.y, sj.z};
+      surv = survives_fp32(P, __ldg(&xy32[tix]), sw, __ldg(&xyq[tix]), a.Si32, Sj32, s,
+                           (int64_t)a.i, j, dx, dy, A, wU, g32, ghits);
+    } else {
+      const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
+      surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), a.Si, Sj, dx, dy, A, u53(wU), ghits);
+    }
+    if (surv) {
+      switch_emit(o, a.id, a.n_out, (uint32_t)j);
+      ++n_dip;
+      if (k == mnn0) a.nn0 = true;
+      if (k == mnn1) a.nn1 = true;
+    }
+  }
+  a.sidx = k;
+  a.Ws = Wk;
+  return true;
+}
+
+// Ends the walk: exchange bonds that the dipolar switch did not keep join the colouring graph.
+// Returns the number of upper neighbours written (dipolar survivors plus exchange-only bonds).
+template <int PREC>
+__device__ __forceinline__ uint32_t walk_end(const DevParams& P, int32_t mnn0, int32_t mnn1,
+                                             const SwitchOut& o, SiteWalk<PREC>& a) {
+  if (P.J != 0.0) {
+    if (mnn0 >= 0 && !a.nn0 && a.xi + 1 < P.Lx) switch_emit(o, a.id, a.n_out, (a.i + 1) | kExchOnly);
+    if (mnn1 >= 0 && !a.nn1 && a.yi + 1 < P.Ly)
+      switch_emit(o, a.id, a.n_out, (a.i + (uint32_t)P.Lx) | kExchOnly);
+  }
+  return a.n_out;
+}
+
+// Switches the half-plane pairs of site i (local index, slot id `id`) at this epoch in one go;
+// returns the number of upper neighbours written.
 template <int PREC>
 __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTable& T,
                                                 uint64_t Wtot, const Sw64* __restrict__ sw,
@@ -264,82 +388,15 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
                                                 const double* __restrict__ s,
                                                 const float4* __restrict__ s32, uint32_t epoch,
                                                 int32_t mnn0, int32_t mnn1, uint32_t i,
-                                                const SwitchOut& o, unsigned long long& n_dip,
-                                                unsigned& ghits, unsigned& g32) {
-  const int32_t yi = (int32_t)site_row(i, P);
-  const int32_t xi = (int32_t)(i - (uint32_t)yi * (uint32_t)P.Lx);
-  double Si[3] = {0.0, 0.0, 0.0};
-  float Si32[3] = {0.f, 0.f, 0.f};
-  if (PREC == 0) {
-    Si[0] = s[i];
-    Si[1] = s[P.N + i];
-    Si[2] = s[2 * P.N + i];
-  } else {
-    const float4 si = s32[i];
-    Si32[0] = si.x;
-    Si32[1] = si.y;
-    Si32[2] = si.z;
+                                                uint32_t id, const SwitchOut& o,
+                                                unsigned long long& n_dip, unsigned& ghits,
+                                                unsigned& g32) {
+  SiteWalk<PREC> a;
+  walk_begin<PREC>(P, s, s32, i, id, a);
+  while (walk_step<PREC>(P, T, Wtot, sw, xyq, xy32, s, s32, epoch, mnn0, mnn1, o, a, n_dip,
+                         ghits, g32)) {
   }
-  uint32_t n_out = 0;
-  bool nn0 = false, nn1 = false;
-  auto emit = [&](uint32_t jv) {
-    if (n_out < (uint32_t)kSlotCap) {
-      o.slot[n_out] = jv;
-    } else {
-      const unsigned long long idx = atomicAdd(o.ovf_n, 1ull);
-      if (idx < o.ovf_cap) {
-        o.ovf[2 * idx] = o.site_id;
-        o.ovf[2 * idx + 1] = jv;
-      } else {
-        set_status(o.status, kStatusCapacity);
-      }
-    }
-    ++n_out;
-    atomicAdd(&o.indeg[jv & kIndexMask], 1u);
-  };
-  int64_t sidx = -1;
-  uint64_t Ws = 0;
-  W4 w;
-  for (uint64_t n = 0;; ++n) {
-    if ((n & 1) == 0) w = philox((uint64_t)i, epoch, n >> 1, kTagSwitch, P.key0, P.key1);
-    const uint64_t wE = (n & 1) ? w.w[2] : w.w[0];
-    const uint64_t wU = (n & 1) ? w.w[3] : w.w[1];
-    const int64_t k = PREC == 1 ? next_candidate_fp32(P, T, sidx, Ws, Wtot, wE, g32, ghits)
-                                : next_candidate(P, T, sidx, Ws, Wtot, wE, ghits);
-    if (k >= P.K) break;
-    const uint32_t d = T.d(k);
-    const int32_t dx = (int16_t)(d & 0xFFFFu), dy = (int32_t)(d >> 16);
-    const uint64_t Wk = T.w(k);
-    const int32_t xj = xi + dx, yj = yi + dy;
-    if (xj >= 0 && xj < P.Lx && yj < P.Ly) {
-      const int64_t j = xj + (int64_t)P.Lx * yj;
-      const uint64_t A = Wk - (k > 0 ? T.w(k - 1) : 0ull);
-      const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
-      bool surv;
-      if (PREC == 1) {
-        const float4 sj = s32[j];
-        const float Sj32[3] = {sj.x, sj.y, sj.z};
-        surv = survives_fp32(P, __ldg(&xy32[tix]), sw, __ldg(&xyq[tix]), Si32, Sj32, s,
-                             (int64_t)i, j, dx, dy, A, wU, g32, ghits);
-      } else {
-        const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-        surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), Si, Sj, dx, dy, A, u53(wU), ghits);
-      }
-      if (surv) {
-        emit((uint32_t)j);
-        ++n_dip;
-        if (k == mnn0) nn0 = true;
-        if (k == mnn1) nn1 = true;
-      }
-    }
-    sidx = k;
-    Ws = Wk;
-  }
-  if (P.J != 0.0) {  // exchange bonds join the colouring graph
-    if (mnn0 >= 0 && !nn0 && xi + 1 < P.Lx) emit((i + 1) | kExchOnly);
-    if (mnn1 >= 0 && !nn1 && yi + 1 < P.Ly) emit((i + (uint32_t)P.Lx) | kExchOnly);
-  }
-  return n_out;
+  return walk_end<PREC>(P, mnn0, mnn1, o, a);
 }
 
 // Sorts one CSR row by neighbour index (insertion sort, in registers up to 64 entries);
