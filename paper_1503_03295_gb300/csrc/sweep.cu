@@ -22,6 +22,11 @@ __global__ void __launch_bounds__(256) k_propose(const DevParams P, uint64_t ste
                : make_double4_32a(0.0, 0.0, 1.0, -1.0);
 }
 
+// In the FP64 form, classes of at most this many sites (the largest colours hold a few dozen)
+// are left to k_resolve, which sweeps them one warp per site: the pairs of a site spread over
+// the lanes, the launch lasts about one pair's FP64 chain instead of a whole row's.
+constexpr uint32_t kSweepWarpSites = 4096;
+
 // One thread per site of the class.  A site whose decision stays inside the error bound is
 // appended to the deferred list of the colour and settled by k_resolve (one warp per site),
 // so that no thread of this kernel runs the long FP64 / double-double evaluations.
@@ -39,6 +44,7 @@ __global__ void __launch_bounds__(128, 8) k_sweep(const DevParams P, const Sw64*
                                                uint32_t* __restrict__ dcnt,
                                                DevCounters* __restrict__ cnt) {
   const uint32_t b = off[colour], e = off[colour + 1];
+  if (PREC == 0 && e - b <= kSweepWarpSites) return;  // swept by k_resolve
   unsigned long long nd = 0;
   for (uint32_t idx = b + blockIdx.x * blockDim.x + threadIdx.x; idx < e;
        idx += gridDim.x * blockDim.x) {
@@ -67,11 +73,13 @@ __global__ void __launch_bounds__(128, 8) k_sweep(const DevParams P, const Sw64*
   }
 }
 
-// Settles the deferred sites of a colour: one warp per site, FP64 then double-double.
+// Settles the deferred sites of a colour: one warp per site, FP64 then double-double.  In the
+// FP64 form a class of at most kSweepWarpSites sites is swept here whole, one warp per site.
 __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* __restrict__ sw,
                                                  double* __restrict__ s, float4* __restrict__ s32,
                                                  const uint32_t* __restrict__ row_ptr,
                                                  const uint32_t* __restrict__ col,
+                                                 const uint32_t* __restrict__ perm,
                                                  const uint32_t* __restrict__ off,
                                                  const uint32_t* __restrict__ defer,
                                                  const uint32_t* __restrict__ dcnt, uint32_t colour,
@@ -79,16 +87,24 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
                                                  int fp32_screened,
                                                  uint8_t* __restrict__ acc,
                                                  DevCounters* __restrict__ cnt) {
-  const uint32_t n = dcnt[colour], b = off[colour];
+  const uint32_t b = off[colour], e = off[colour + 1];
+  const bool whole = !fp32_screened && e - b <= kSweepWarpSites;  // uniform
+  const uint32_t n = whole ? e - b : dcnt[colour];
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned long long ndd = 0;
   for (uint32_t q = warp; q < n; q += nwarps) {
     SiteCtx c;
-    load_site(P, c, defer[b + q], s);
-    take_proposal(c, prop);
-    int d = fp32_screened ? accept_fp64_warp(P, c, sw, s, row_ptr, col, lane) : 2;
+    load_site(P, c, whole ? perm[b + q] : defer[b + q], s);
+    if (!take_proposal(c, prop)) {  // only a whole-class site can lack a move
+      if (lane == 0) acc[c.i] = 0;
+      __syncwarp();
+      continue;
+    }
+    int d = 2;
+    if (whole && c.u == 0.0) d = 1;
+    else if (fp32_screened || whole) d = accept_fp64_warp(P, c, sw, s, row_ptr, col, lane);
     if (d == 2) {
       ++ndd;
       d = accept_dd_warp(P, c, s, row_ptr, col, lane) ? 1 : 0;
@@ -96,7 +112,8 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
     if (lane == 0) write_site(P, c, d == 1, s, fp32_screened ? s32 : nullptr, acc);
     __syncwarp();
   }
-  if (lane == 0 && ndd && fp32_screened) atomicAdd(&cnt->guard_fp64, ndd);
+  // deferred FP64-form sites were counted by k_sweep already
+  if (lane == 0 && ndd && (fp32_screened || whole)) atomicAdd(&cnt->guard_fp64, ndd);
 }
 
 }  // namespace
@@ -110,7 +127,7 @@ cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32
   if (e != cudaSuccess) return e;
   k_propose<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P, step, prop);
   ++*launches;
-  const unsigned nres = (unsigned)(2 * num_sms());
+  const unsigned nres = (unsigned)(4 * num_sms());
   // one launch per colour in ascending order; a class holds about N / g sites.  The grid is a
   // whole number of blocks per SM (every SM gets the same share of a class: the FP64 form is
   // bound by each SM's FP64 pipe) and at most the resident 8 per SM of __launch_bounds__.
@@ -127,8 +144,8 @@ cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32
     else
       k_sweep<0><<<(unsigned)nb, 128, 0, st>>>(P, t.sw64, t.sw32, s, s32, row_ptr, col, perm,
                                                 off, c, prop, acc, defer, dcnt, cnt);
-    k_resolve<<<nres, 128, 0, st>>>(P, t.sw64, s, s32, row_ptr, col, off, defer, dcnt, c, prop,
-                                    precision == 1 ? 1 : 0, acc, cnt);
+    k_resolve<<<nres, 128, 0, st>>>(P, t.sw64, s, s32, row_ptr, col, perm, off, defer, dcnt, c,
+                                    prop, precision == 1 ? 1 : 0, acc, cnt);
     *launches += 2;
   }
   return cudaGetLastError();
