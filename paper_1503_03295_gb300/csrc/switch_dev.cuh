@@ -399,25 +399,44 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
   return walk_end<PREC>(P, mnn0, mnn1, o, a);
 }
 
-// Sorts one CSR row by neighbour index (insertion sort, in registers up to 64 entries);
-// returns the number of dipolar entries of the row.
+// Compare-exchange on the neighbour index (the exchange flag travels with its entry).
+__device__ __forceinline__ void row_ce(uint32_t& a, uint32_t& b) {
+  const bool sw = (a & kIndexMask) > (b & kIndexMask);
+  const uint32_t lo = sw ? b : a, hi = sw ? a : b;
+  a = lo;
+  b = hi;
+}
+
+// Sorts one CSR row by neighbour index; returns the number of dipolar entries of the row.
+// Rows of at most 32 entries go through a bitonic network in registers (padded with
+// 0xFFFFFFFF, whose index sorts after every site), longer ones through an insertion sort in
+// place.  Neighbour indices inside a row are distinct, so the order is unique.
 __device__ __forceinline__ unsigned sort_row(uint32_t* __restrict__ r, uint32_t n) {
   unsigned nd = 0;
-  constexpr uint32_t kLocal = 64;
-  if (n <= kLocal) {
-    uint32_t v[kLocal];
-    for (uint32_t a = 0; a < n; ++a) {
-      const uint32_t x = r[a];
-      uint32_t c = a;
-      while (c > 0 && (v[c - 1] & kIndexMask) > (x & kIndexMask)) {
-        v[c] = v[c - 1];
-        --c;
+  if (n <= 32) {
+    uint32_t v[32];
+#pragma unroll
+    for (int a = 0; a < 32; ++a) v[a] = (uint32_t)a < n ? r[a] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 32; ++a) {
+          const int l = a ^ j;
+          if (l > a) {
+            if ((a & k) == 0) row_ce(v[a], v[l]);
+            else row_ce(v[l], v[a]);
+          }
+        }
       }
-      v[c] = x;
     }
-    for (uint32_t a = 0; a < n; ++a) {
-      r[a] = v[a];
-      nd += (v[a] & kExchOnly) ? 0u : 1u;
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      if ((uint32_t)a < n) {
+        r[a] = v[a];
+        nd += (v[a] & kExchOnly) ? 0u : 1u;
+      }
     }
   } else {
     for (uint32_t a = 1; a < n; ++a) {
