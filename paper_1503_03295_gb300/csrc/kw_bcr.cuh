@@ -407,6 +407,28 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
         ok = grid_sync(V.bar, V.status, V.ns_limit);
         c = next_bucket(ct);
       }
+      // the buckets below that hold at most a quarter of the grid's threads each run with no
+      // barrier between them: every thread takes their items in descending colour order and
+      // waits (bounded) for the listed neighbours, all of larger colour, hence taken up
+      // earlier by their own threads; one grid barrier publishes the run
+      if (ok && c >= 0) {
+        int cm = c;
+        while (cm >= 0 && start[cm + 1] - start[cm] <= nth / 4) --cm;
+        if (cm < c) {
+          const uint32_t hi = start[c + 1], lo = start[cm + 1];
+          bool mine = true;
+          int cb = c;
+          for (uint32_t q = gtid; q < hi - lo && mine; q += nth) {
+            const uint32_t pos = hi - 1 - q;
+            while (pos < start[cb]) --cb;
+            KwItem it;
+            kw_item_fetch(it, V, pos);
+            mine = recolour(it, cb);
+          }
+          ok = grid_sync(V.bar, V.status, V.ns_limit);
+          c = next_bucket(cm + 1);
+        }
+      }
       KwItem it;
       it.gv = kNone;
       if (c >= 0 && gtid < start[c + 1] - start[c]) kw_item_fetch(it, V, start[c] + gtid);
