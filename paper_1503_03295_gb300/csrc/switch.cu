@@ -13,7 +13,7 @@ namespace {
 // ends takes up the next claimed site at once, so that the lanes of a warp stay busy although
 // the number of candidates differs from site to site (Poisson, mean about 14 at T = 0.6D).
 template <int PREC>
-__global__ void __launch_bounds__(256, 4) k_switch(const DevParams P, const uint64_t* __restrict__ W,
+__global__ void __launch_bounds__(256, 5) k_switch(const DevParams P, const uint64_t* __restrict__ W,
                                                 const uint32_t* __restrict__ disp,
                                                 const Sw64* __restrict__ sw64,
                                                 const double* __restrict__ xyq,
