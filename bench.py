@@ -157,7 +157,7 @@ class ClockSampler:
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal
 # DRAM bytes (read + write) of one FP64 sweep launch (one colour class) at L=2304, T=0.6D,
 # seed 0, from one ncu capture (profiles/dram_traffic_L2304_T0.6.md); valid for that workload
-SWEEP64_TRAFFIC_PER_CLASS = 98.3e6
+SWEEP64_TRAFFIC_PER_CLASS = 99.3e6
 
 
 def low_levels(g, M):

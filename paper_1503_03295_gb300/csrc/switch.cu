@@ -12,8 +12,10 @@ namespace {
 // Persistent: each warp claims 32 sites at a time from a global counter, and a lane whose walk
 // ends takes up the next claimed site at once, so that the lanes of a warp stay busy although
 // the number of candidates differs from site to site (Poisson, mean about 14 at T = 0.6D).
+// Five blocks per SM for the FP32-screened form (48 registers); four for the FP64 form, which
+// takes the same time there with half the register spills.
 template <int PREC>
-__global__ void __launch_bounds__(256, 5) k_switch(const DevParams P, const uint64_t* __restrict__ W,
+__global__ void __launch_bounds__(256, PREC == 1 ? 5 : 4) k_switch(const DevParams P, const uint64_t* __restrict__ W,
                                                 const uint32_t* __restrict__ disp,
                                                 const Sw64* __restrict__ sw64,
                                                 const double* __restrict__ xyq,
