@@ -26,7 +26,7 @@ METRIC = "spin updates/s (switch+colour+sweep) at L=2304; FP32-guarded vs FP64; 
 UNIT = "spin updates/s"
 FALLBACK_HBM_GBS = 6800.0
 # switching candidates per site (half plane) for independent uniform spins, from the closed
-# form of the survival statistics (planning values)
+# form of the survival statistics (planning values of the work per site)
 CANDIDATES_PER_SITE = {0.2: 30.5, 0.3: 23.1, 0.4: 19.0, 0.5: 16.3, 0.6: 14.4, 0.8: 11.8,
                        1.2: 9.0, 1.5: 7.7}
 L2_BYTES = 129 * 1024 * 1024
@@ -156,7 +156,8 @@ class ClockSampler:
 
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal
 # DRAM bytes (read + write) of one FP64 sweep launch (one colour class) at L=2304, T=0.6D,
-# seed 0, from one ncu capture (profiles/dram_traffic_L2304_T0.6.md); valid for that workload
+# seed 0: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture, averaged over the
+# class launches; valid for that workload only
 SWEEP64_TRAFFIC_PER_CLASS = 99.3e6
 
 
@@ -170,8 +171,8 @@ def low_levels(g, M):
 
 
 def algorithmic_bytes(k, M, p0):
-    """Bytes per spin update that each phase must move at least once:
-    switch + CSR 40 + 16k; colouring + classes: the first p0 levels read the rows once and write
+    """Bytes per spin update that each phase must move at least once, k the mean degree, M the
+    KW levels and p0 the block-local ones: switch + CSR 40 + 16k; colouring + classes: the first p0 levels read the rows once and write
     the colours (4 + 4k + 9), every later level half the rows and colours (4 + 2k), classes 12;
     sweep 60 + 8k."""
     colour = (4 + 4 * k + 9 if p0 else 0) + (M - p0) * (4 + 2 * k) + 12
@@ -179,9 +180,11 @@ def algorithmic_bytes(k, M, p0):
 
 
 def algorithmic_flops(k, cand):
-    """FP64 operations per spin update of the FP64 form: 70 per switching
+    """FP64 operations per spin update of the FP64 form, planning figures: 70 per switching
     candidate (one logarithm, one expm1, the pair energy) and 120 per pair of the sweep
-    (two pair energies, two pseudointeraction terms); the colouring has none."""
+    (two pair energies, two pseudointeraction terms, a log1mexp counted as two
+    transcendentals); the colouring has none.  The kernels issue fewer (about 40 per candidate
+    and 39 per pair), so these fractions measure work done against the plan."""
     return {"switch": 70.0 * cand, "colour": 0.0, "sweep": 120.0 * k}
 
 
