@@ -172,9 +172,9 @@ def low_levels(g, M):
 
 def algorithmic_bytes(k, M, p0):
     """Bytes per spin update that each phase must move at least once, k the mean degree, M the
-    KW levels and p0 the block-local ones: switch + CSR 40 + 16k; colouring + classes: the first p0 levels read the rows once and write
-    the colours (4 + 4k + 9), every later level half the rows and colours (4 + 2k), classes 12;
-    sweep 60 + 8k."""
+    KW levels and p0 the block-local ones: switch + CSR 40 + 16k; colouring + classes: the
+    first p0 levels read the rows once and write the colours (4 + 4k + 9), every later level
+    half the rows and colours (4 + 2k), classes 12; sweep 60 + 8k."""
     colour = (4 + 4 * k + 9 if p0 else 0) + (M - p0) * (4 + 2 * k) + 12
     return {"switch": 40 + 16 * k, "colour": colour, "sweep": 60 + 8 * k}
 
