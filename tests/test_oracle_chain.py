@@ -150,3 +150,77 @@ def test_extended_precision_path_gives_the_same_trajectory():
     O.set_guard_scale(1.0)
     assert np.array_equal(runs[0][0], runs[1][0])
     assert runs[1][1] > 1000 * max(runs[0][1], 1)
+
+
+def _bond_count(Lx, Ly):
+    # open Lx x Ly lattice: Ly rows of Lx - 1 horizontal bonds, Lx columns of Ly - 1 vertical
+    return Lx * (Ly - 1) + Ly * (Lx - 1)
+
+
+@pytest.mark.parametrize("Lx,Ly,J", [(5, 3, 1.0), (1, 6, 0.7), (4, 4, -2.5), (7, 1, 1.0)])
+def test_exchange_energy_closed_forms(Lx, Ly, J):
+    # The exchange term of Eq. (6), -J sum_<ij> S_i.S_j over nearest-neighbour bonds.
+    # All spins parallel: every bond gives -J.  Neel checkerboard along z: every bond joins
+    # opposite spins (+J).  In-plane spins alternating between +x and +y by column: the
+    # horizontal bonds are orthogonal (0) and the vertical bonds parallel (-J each).
+    N = Lx * Ly
+    x, y = np.arange(N) % Lx, np.arange(N) // Lx
+    nb = _bond_count(Lx, Ly)
+    ch = O.Chain(O.make_params(Lx, Ly, T=0.5, J=J, seed=1))
+    ch.set_spins(np.concatenate([np.zeros(2 * N), np.ones(N)]))
+    assert ch.observables()["e_exchange"] == pytest.approx(-J * nb, rel=1e-15)
+    sz = np.where((x + y) % 2 == 0, 1.0, -1.0)
+    ch.set_spins(np.concatenate([np.zeros(2 * N), sz]))
+    assert ch.observables()["e_exchange"] == pytest.approx(J * nb, rel=1e-15)
+    even = (x % 2 == 0).astype(float)
+    ch.set_spins(np.concatenate([even, 1.0 - even, np.zeros(N)]))
+    assert ch.observables()["e_exchange"] == pytest.approx(-J * Lx * (Ly - 1), rel=1e-15,
+                                                           abs=1e-15)
+
+
+def test_exchange_energy_brute_force_neighbour_search():
+    # Random spins on a 4 x 3 lattice: the exchange energy against a sum over every pair of
+    # sites whose displacement has |dx| + |dy| = 1 (an independent neighbour search).
+    Lx, Ly, J = 4, 3, 1.3
+    N = Lx * Ly
+    rng = np.random.default_rng(5)
+    s = rng.normal(size=(N, 3))
+    s /= np.linalg.norm(s, axis=1, keepdims=True)
+    x, y = np.arange(N) % Lx, np.arange(N) // Lx
+    e = 0.0
+    for i in range(N):
+        for j in range(i + 1, N):
+            if abs(int(x[j]) - int(x[i])) + abs(int(y[j]) - int(y[i])) == 1:
+                e -= J * float(s[i] @ s[j])
+    ch = O.Chain(O.make_params(Lx, Ly, T=0.5, J=J, seed=2))
+    ch.set_spins(s.T.reshape(-1))
+    assert ch.observables()["e_exchange"] == pytest.approx(e, rel=1e-14)
+
+
+def test_two_spin_exchange_and_switched_energy():
+    # A 2 x 1 lattice with J != 0: e_exchange = -J S_1.S_2 exactly, and the switched energy
+    # H' of Eq. (4) adds the pseudointeraction Vbar of Eq. (3) when the dipolar pair survives.
+    # With D = 0 the exchange bond is the only term (no pair can survive).
+    beta, J = 1.5, 0.8
+    for D in (1.0, 0.0):
+        ch = O.Chain(O.make_params(2, 1, T=1 / beta, J=J, D=D, seed=2))
+        seen = set()
+        for e in range(80):
+            ch.switch_epoch(e)
+            o = ch.observables(full=True)
+            s = ch.spins().reshape(3, 2)
+            dot = float(s[:, 0] @ s[:, 1])
+            assert o["e_exchange"] == pytest.approx(-J * dot, rel=1e-15)
+            V = D * (dot - 3 * s[0, 0] * s[0, 1])
+            vbar = 0.0
+            if o["n_edges"]:
+                vm = O.vmax(D, 1)
+                vbar = V - np.log1p(-np.exp(beta * (V - vm))) / beta
+            assert o["e_switched"] == pytest.approx(vbar - J * dot, rel=1e-13)
+            assert o["e_full"] == pytest.approx(V - J * dot, rel=1e-13, abs=1e-15)
+            seen.add(o["n_edges"])
+            if D == 0.0:
+                assert o["n_edges"] == 0
+            ch.sweep(1)
+        if D == 1.0:
+            assert seen == {0, 1}  # both switch outcomes were exercised
