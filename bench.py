@@ -57,6 +57,15 @@ def parse():
                     help="batched arm: keep the default launch tuning")
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the batched arm and print its object (profiling)")
+    ap.add_argument("--long-steps", type=int, default=500,
+                    help="MC steps of the long L=2304 FP64 run (all-step and last-half rates); "
+                         "0 skips it")
+    ap.add_argument("--prec-steps", type=int, default=1000,
+                    help="MC steps per run of the L=1024 FP32-guarded vs FP64 comparison at "
+                         "T = 0.4 D and 0.8 D; 0 skips it")
+    ap.add_argument("--prec-L", type=int, default=1024)
+    ap.add_argument("--no-kw-bound", action="store_true",
+                    help="skip t_R of both colour-reduction variants against Eq. (5)'s bound")
     return ap.parse_args()
 
 
@@ -154,11 +163,26 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal
-# DRAM bytes (read + write) of one FP64 sweep launch (one colour class) at L=2304, T=0.6D,
-# seed 0: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture, averaged over the
-# class launches; valid for that workload only
-SWEEP64_TRAFFIC_PER_CLASS = 99.3e6
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal: context only
+# FP64 sweep kernels, per pair of the switched graph and per spin update, from one ncu capture
+# of the current kernels on a smaller lattice at T = 0.6 D (DRAM bytes and executed FP64
+# thread-instructions scale with the updates and pairs, not with L): see the named profile
+SWEEP64_EXECUTED_FP64_PER_PAIR = None
+SWEEP64_DRAM_BYTES_PER_UPDATE = None
+SWEEP64_TRAFFIC_T = 0.6
+SWEEP64_EXECUTED_SOURCE = "profiles/k_sweep_fp64_L1024_T0.6.md"
+
+
+def fp64_peak(local):
+    """Measured FP64 throughput of this GPU (sco_probe_fp64: independent FMA chains filling
+    every SM), with the SM clock sampled while it ran."""
+    import paper_1503_03295_gb300 as sco
+
+    with ClockSampler(local) as clk:
+        r = sco.probe_fp64(8192)
+    r["gflops"] = r["flops"] / 1e9
+    r["clocks"] = clk.summary()
+    return r
 
 
 def low_levels(g, M):
@@ -194,17 +218,18 @@ def phase_ms(ph):
             "sweep": ph["sweep_ms"] / max(ph["sweep_calls"], 1)}
 
 
-def rooflines(per_step, N, k, M, p0, cand, hbm, how, fp64):
-    """HBM roofline of every phase and, for the FP64 form, the FP64-ALU roofline."""
+def rooflines(per_step, N, k, M, p0, cand, hbm, how, fp64_gflops=None):
+    """HBM roofline of every phase and, for the FP64 form (fp64_gflops: the measured FP64
+    peak), the FP64-ALU roofline against the planning operation counts."""
     ab = algorithmic_bytes(k, M, p0)
     af = algorithmic_flops(k, cand)
     out = {}
     for ph, ms in per_step.items():
         gbs = ab[ph] * N / (ms / 1e3) / 1e9
         r = {"hbm_achieved_GBs": gbs, "hbm_frac": gbs / hbm, "algorithmic_bytes_per_update": ab[ph]}
-        if fp64 and af[ph] > 0:
+        if fp64_gflops and af[ph] > 0:
             gf = af[ph] * N / (ms / 1e3) / 1e9
-            r.update({"fp64_achieved_GFLOPs": gf, "fp64_frac": gf / FP64_NOMINAL_GFLOPS,
+            r.update({"fp64_achieved_GFLOPs": gf, "fp64_frac": gf / fp64_gflops,
                       "algorithmic_fp64_ops_per_update": af[ph]})
         out[ph] = r
     return out
@@ -251,7 +276,7 @@ def run_ours(args, rank, world, local):
         launches = lat.observables()["kernel_launches"] - l0
         return ms, ph, launches
 
-    out = {}
+    out = {"fp64_peak": fp64_peak(local)}
     lat = lattice(sco.FP64)
     with ClockSampler(local) as clk:
         ms, ph, launches = timed(lat, args.steps, args.warmup, timing=True)
@@ -289,8 +314,123 @@ def run_ours(args, rank, world, local):
         out["fp32"] = dict(ms=ms32, phases=ph32, launches=l32, obs=lat32.observables())
         lat32.close()
         del lat32
+    if args.long_steps > 0:
+        out["long"] = run_long(args, rank, world, dev, stream)
+    if args.prec_steps > 0:
+        out["precision"] = run_precision(args, rank, world, dev, stream)
+    if not args.no_kw_bound:
+        out["kw_bound"] = [kw_bound(L, args.T, rank_seed(args.seed, rank), stream)
+                           for L in sorted({256, args.L})]
     if not args.no_batch:
         out["batch"] = run_batch(args, rank, local)
+    return out
+
+
+def _timed_steps(lat, K, dev, stream):
+    """Device time (ms) of K MC steps of a lattice, CUDA events on its stream."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        lat.sweep(K)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1)
+
+
+def run_long(args, rank, world, dev, stream):
+    """The long FP64 run at the benchmark lattice from the random start: rate over all steps
+    and over the second half (spins order as the run goes on, so the graph's mean degree
+    grows), with the mean degree at the end."""
+    import paper_1503_03295_gb300 as sco
+
+    K = args.long_steps
+    lat = sco.Lattice(sco.make_params(args.L, T=args.T, seed=rank_seed(args.seed, rank)),
+                      stream=stream.cuda_stream)
+    k0 = None
+    lat.sweep(1)
+    k0 = 2.0 * lat.observables()["n_edges"] / lat.N
+    first = K // 2
+    ms_a = max_over_ranks(_timed_steps(lat, first - 1, dev, stream), world, dev)
+    ms_b = max_over_ranks(_timed_steps(lat, K - first, dev, stream), world, dev)
+    o = lat.observables()
+    lat.close()
+    N = args.L * args.L
+    # the first step (untimed, before the events) is counted at the first half's rate
+    ms_all = (ms_a + ms_b) * K / (K - 1)
+    return {"steps": K, "precision": "fp64",
+            "value_all_steps": whole_job_rate(N, K, world, ms_all),
+            "value_last_half": whole_job_rate(N, K - first, world, ms_b),
+            "ms_per_step_all": ms_all / K, "ms_per_step_last_half": ms_b / (K - first),
+            "mean_degree_first_step": k0, "mean_degree_end": 2.0 * o["n_edges"] / N,
+            "max_degree_end": o["max_degree"], "n_colours_end": o["n_colours"],
+            "e_switched_per_spin_end": o["e_switched"] / N,
+            "workload": "L=%d, J=0, D=1, T=%gD, seed %d, n_sw=1, FP64, %d MC steps from the "
+                        "random start" % (args.L, args.T, args.seed, K)}
+
+
+def run_precision(args, rank, world, dev, stream):
+    """The precision workload: FP32-guarded against FP64 on the same seeds at T = 0.4 D and
+    0.8 D, each run the same number of MC steps; the two forms take identical decisions, so
+    their spins must end bit-identical (energy then equal to summation order)."""
+    import numpy as np
+    import paper_1503_03295_gb300 as sco
+
+    L, K = args.prec_L, args.prec_steps
+    N = L * L
+    res = {"L": L, "steps": K, "runs": []}
+    for T in (0.4, 0.8):
+        row = {"T": T}
+        spins = {}
+        for name, prec in (("fp64", sco.FP64), ("fp32_guarded", sco.FP32_GUARDED)):
+            lat = sco.Lattice(sco.make_params(L, T=T, seed=1 + rank, precision=prec),
+                              stream=stream.cuda_stream)
+            lat.sweep(1)
+            ms = max_over_ranks(_timed_steps(lat, K - 1, dev, stream), world, dev)
+            o = lat.observables()
+            spins[name] = lat.spins()
+            lat.close()
+            row[name] = {"value": whole_job_rate(N, K - 1, world, ms),
+                         "ms_per_step": ms / (K - 1), "e_switched": o["e_switched"],
+                         "guard_hits_fp32": o["guard_hits_fp32"],
+                         "guard_hits_fp64": o["guard_hits_fp64"],
+                         "mean_degree_end": 2.0 * o["n_edges"] / N}
+        row["identical_spins"] = bool(np.array_equal(spins["fp64"], spins["fp32_guarded"]))
+        e64, e32 = row["fp64"]["e_switched"], row["fp32_guarded"]["e_switched"]
+        row["energy_rel_diff"] = abs(e32 - e64) / max(abs(e64), 1e-300)
+        row["speedup_fp32_guarded"] = row["fp32_guarded"]["value"] / row["fp64"]["value"]
+        res["runs"].append(row)
+    res["workload"] = ("L=%d, J=0, D=1, T in {0.4, 0.8} D, seed 1, n_sw=1, %d MC steps per "
+                       "form from the random start (the first untimed)" % (L, K))
+    return res
+
+
+def kw_bound(L, T, seed, stream):
+    """t_R of the colouring for both colour reductions on the same switched graph (the first
+    graph of the run), against Eq. (5)'s (Delta + 1) log2(N / (Delta + 1)) and the level
+    count M = ceil(log2 ceil(N / (Delta + 1)))."""
+    import math
+    import paper_1503_03295_gb300 as sco
+
+    out = {"L": L, "T": T}
+    for variant, name in ((0, "modified_bcr"), (1, "plain_bcr")):
+        lat = sco.Lattice(sco.make_params(L, T=T, seed=seed, colour_variant=variant),
+                          stream=stream.cuda_stream)
+        lat.colour()
+        o = lat.observables()
+        lat.close()
+        g = o["max_degree"] + 1
+        N = L * L
+        G = -(-N // g)
+        M = 0
+        while (1 << M) < G:
+            M += 1
+        out[name] = {"t_R": o["kw_rounds"], "n_colours": o["n_colours"]}
+        out.update({"max_degree": o["max_degree"], "levels_M": M, "g_times_M": g * M,
+                    "eq5_bound": g * math.log2(N / g) if N > g else 0.0})
+    out["plain_over_modified"] = out["plain_bcr"]["t_R"] / max(out["modified_bcr"]["t_R"], 1)
     return out
 
 
@@ -404,20 +544,34 @@ def main():
         levels += 1
     cand = CANDIDATES_PER_SITE.get(round(args.T, 3), 14.4)
     hbm, how = peaks()
+    fpk = res["fp64_peak"]
     per_step = phase_ms(f64["phases"])
     p0 = low_levels(g, levels)
-    roof = rooflines(per_step, N, k, levels, p0, cand, hbm, how, True)
+    roof = rooflines(per_step, N, k, levels, p0, cand, hbm, how, fpk["gflops"])
     dom = max(per_step, key=per_step.get)
     if roof[dom].get("fp64_achieved_GFLOPs"):
-        traffic = None
-        if dom == "sweep" and args.L == 2304 and abs(args.T - 0.6) < 1e-9 and args.seed == 0:
-            traffic = SWEEP64_TRAFFIC_PER_CLASS * obs["n_colours"]  # bytes per step (all classes)
         primary = {"bound": "alu", "kernel": dom, "achieved": roof[dom]["fp64_achieved_GFLOPs"],
-                   "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                   "frac": roof[dom]["fp64_frac"], "traffic": traffic,
-                   "traffic_unit": "DRAM bytes per step of the phase (ncu, full size)",
-                   "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
+                   "peak": fpk["gflops"], "unit": "GFLOP/s",
+                   "frac": roof[dom]["fp64_frac"], "traffic": None,
+                   "peak_source": "measured in this run: sco_probe_fp64, independent FP64 FMA "
+                                  "chains filling every SM (2 flops per FMA), SM clock %s MHz" % (
+                                      fpk["clocks"]["sm_mhz"],),
                    "algorithmic_fp64_ops_per_update": roof[dom]["algorithmic_fp64_ops_per_update"]}
+        if dom == "sweep" and SWEEP64_EXECUTED_FP64_PER_PAIR:
+            # the same phase against the FP64 instructions its kernels execute (ncu count of a
+            # class launch per pair of the switched graph), at the measured FMA issue rate
+            ex = SWEEP64_EXECUTED_FP64_PER_PAIR * k
+            rate = ex * N / (per_step["sweep"] / 1e3)
+            primary["executed"] = {
+                "fp64_lane_inst_per_update": ex, "achieved_inst_per_s": rate,
+                "peak_inst_per_s": fpk["dfma_per_s"], "frac": rate / fpk["dfma_per_s"],
+                "source": SWEEP64_EXECUTED_SOURCE}
+            if abs(args.T - SWEEP64_TRAFFIC_T) < 1e-9 and SWEEP64_DRAM_BYTES_PER_UPDATE:
+                primary["traffic"] = SWEEP64_DRAM_BYTES_PER_UPDATE * N
+                primary["traffic_unit"] = ("DRAM bytes per step of the sweep phase: ncu bytes "
+                                           "per spin update of the same kernels on a smaller "
+                                           "lattice at this T, times N")
+                primary["traffic_source"] = SWEEP64_EXECUTED_SOURCE
     else:
         primary = {"bound": "hbm", "kernel": dom, "achieved": roof[dom]["hbm_achieved_GBs"],
                    "peak": hbm, "unit": "GB/s", "frac": roof[dom]["hbm_frac"], "traffic": None,
@@ -449,9 +603,15 @@ def main():
         line["fp32_guarded"] = {
             "value": whole_job_rate(N, K, world, f32["ms"]), "ms_per_step": f32["ms"] / K,
             "gpu_launches": f32["launches"], "phases_ms_per_step": p32,
-            "roofline_phases": rooflines(p32, N, k, levels, p0, cand, hbm, how, False),
+            "roofline_phases": rooflines(p32, N, k, levels, p0, cand, hbm, how, None),
             "guard_hits_fp32": f32["obs"]["guard_hits_fp32"],
             "guard_hits_fp64": f32["obs"]["guard_hits_fp64"]}
+    line["fp64_peak"] = {"gflops": fpk["gflops"], "dfma_per_s": fpk["dfma_per_s"],
+                         "expm1_per_s": fpk["expm1_per_s"], "log_per_s": fpk["log_per_s"],
+                         "clocks": fpk["clocks"], "nominal_gflops": FP64_NOMINAL_GFLOPS}
+    for key in ("long", "precision", "kw_bound"):
+        if key in res:
+            line[key] = res[key]
     if "batch" in res:
         line["batched"] = res["batch"]
     if not args.no_cpu and world == 1:
@@ -482,9 +642,11 @@ def reference_arm(args, rank, world):
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": "L=%d open lattice, J=0, D=1, T=%gD, seed %d, n_sw=1, FP64" % (
-            args.L, args.T, args.seed), "L": args.L, "N": args.L * args.L, "T": args.T,
-            "precision": "fp64"},
+        "config": {"workload": "L=%d open lattice, J=0, D=1, T=%gD, seed %d, n_sw=1, FP64 (a "
+                               "bounded sample of the L=%d workload: same per-site work)" % (
+                                   L, args.T, args.seed, args.L),
+                   "L": L, "N": L * L, "T": args.T, "precision": "fp64",
+                   "sample_of": {"L": args.L, "N": args.L * args.L}},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -160,11 +160,13 @@ sco_status sco_get_timing(sco_ctx* c, double ms[3], int64_t calls[3]);
  * working memory is one fixed device array inside the library, sized for
  * n <= SCO_KW_STATIC_MAX_VERTICES (8 MiB + 512 B, held on every device that loads the
  * library until the process exits); larger n returns SCO_EINVAL before any device work.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress)
- * and the launch occupancy; make that first call before any stream capture.  Every call
- * reuses the same array (the control block is cleared on each call), so calls that overlap
- * on the GPU, from any stream or thread, race: serialise them.  Synchronises `stream`;
- * returns SCO_ETIMEOUT if a bounded device-side wait gave up.  No allocation of any kind. */
+ * The first call on a device also does a one-time set-up with that device current: it
+ * looks up that array's device address (cudaGetSymbolAddress) and the launch occupancy;
+ * make that first call before any stream capture begins.  Every call reuses the same array
+ * (the control block is cleared on each call), so calls that overlap on the GPU, from any
+ * stream or thread, race: serialise them.  Every call copies max_degree and t_R back to the
+ * host and synchronises `stream` before it returns; it returns SCO_ETIMEOUT if a bounded
+ * device-side wait gave up.  No allocation of any kind. */
 #define SCO_KW_STATIC_MAX_VERTICES (1 << 20)
 sco_status sco_kw_colour_static(const uint32_t* row_ptr, const uint32_t* col, int64_t n,
                                 int32_t variant, uint32_t* colour, int32_t* max_degree,
@@ -243,6 +245,10 @@ sco_status sco_batch_info(sco_batch* b, int64_t* total_sites, int64_t* steps_don
 /* Waits for the batch's stream; returns the sticky device status. */
 sco_status sco_batch_sync(sco_batch* b);
 
+/* The same bound for the batch's kernels (grid barriers of the persistent sweep and of the
+ * colouring, neighbour waits); drops the captured graphs.  Synchronises. */
+sco_status sco_batch_set_wait_limit(sco_batch* b, uint64_t ns);
+
 /* Self-test of the library's own elementary function: the branch-free expm1 for x <= 0.35 used
  * by the FP64 decisions of the switch (argument reduction by ln 2, a degree-8
  * polynomial on |r| <= 0.35, -1 below x = -40), stated relative error bound 2^-42, which those
@@ -270,8 +276,26 @@ sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t degree, doub
 sco_status sco_selftest_log(int64_t n, uint64_t seed, double* max_rel_err,
                             double* max_rel_diff_cuda);
 
+/* FP64 throughput probe of the current device (no counterpart in the paper; it measures the
+ * peak that the FP64 forms of the switch and sweep are held against).  Three timed launches,
+ * each filling every SM with resident 256-thread blocks whose threads advance 8 independent
+ * chains: out[0] = FP64 FMA lane-operations per second (FLOP/s = 2 out[0]) over `iters` FMA
+ * steps per chain; out[1] = evaluations per second of the library's expm1 (degree 6, the
+ * sweep decisions' one) and out[2] of its log, each chain step being one evaluation plus one
+ * FMA, over iters / 12 steps.  iters in [1, 2^30].  Synchronous, on the legacy default
+ * stream of the current device; allocates 8 bytes. */
+sco_status sco_probe_fp64(int64_t iters, double out[3]);
+
 /* Waits for the context's stream; returns the sticky device status. */
 sco_status sco_sync(sco_ctx* c);
+
+/* Bound (ns) of every device-side wait of this context's kernels (the grid barriers and
+ * neighbour waits of the colouring, Sec. 2.3.3); default 2 s, at most 1 h.  A wait that runs
+ * past it gives up, the kernel returns, and SCO_ETIMEOUT becomes the context's sticky
+ * status: sco_sync and every later call return it, and the context does no further work (it
+ * must be destroyed).  Limits below 1 ms are checked on every spin of a wait.  Used by tests
+ * of the failure path; there is no counterpart in the paper.  Synchronises. */
+sco_status sco_set_wait_limit(sco_ctx* c, uint64_t ns);
 
 const char* sco_strerror(sco_status s);
 

@@ -88,6 +88,8 @@ def load():
         "sco_set_timing": ([vp, C.c_int32], st),
         "sco_get_timing": ([vp, vp, vp], st),
         "sco_sync": ([vp], st),
+        "sco_set_wait_limit": ([vp, C.c_uint64], st),
+        "sco_batch_set_wait_limit": ([vp, C.c_uint64], st),
         "sco_kw_colour_static": ([vp, vp, C.c_int64, C.c_int32, vp, C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], st),
         "sco_strerror": ([C.c_int], C.c_char_p),
@@ -113,6 +115,7 @@ def load():
                               C.POINTER(C.c_double)], st),
         "sco_selftest_expm1": ([C.c_int64, C.c_uint64, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)], st),
+        "sco_probe_fp64": ([C.c_int64, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -164,6 +167,15 @@ def selftest_log(n=1 << 24, seed=1):
     a, b = C.c_double(), C.c_double()
     _check(load().sco_selftest_log(int(n), int(seed), C.byref(a), C.byref(b)), "sco_selftest_log")
     return a.value, b.value
+
+
+def probe_fp64(iters=8192):
+    """Measured FP64 throughput of the current device (see sco_probe_fp64): FMA lane-operations,
+    library expm1 (degree 6) and log evaluations per second."""
+    out = np.zeros(3)
+    _check(load().sco_probe_fp64(int(iters), _ptr(out)), "sco_probe_fp64")
+    return {"dfma_per_s": float(out[0]), "flops": 2.0 * float(out[0]),
+            "expm1_per_s": float(out[1]), "log_per_s": float(out[2])}
 
 
 def make_params(Lx, Ly=None, T=1.0, D=1.0, J=0.0, seed=0, n_sw=1, precision=FP64,
@@ -227,6 +239,10 @@ class Lattice:
 
     def sync(self):
         _check(load().sco_sync(self._h), "sco_sync")
+
+    def set_wait_limit(self, ns):
+        """Bound (ns) of every device-side wait (see sco_set_wait_limit)."""
+        _check(load().sco_set_wait_limit(self._h, int(ns)), "sco_set_wait_limit")
 
     # ---- data -----------------------------------------------------------------------
     def spins(self):
@@ -348,6 +364,9 @@ class Batch:
 
     def sync(self):
         _check(load().sco_batch_sync(self._h), "sco_batch_sync")
+
+    def set_wait_limit(self, ns):
+        _check(load().sco_batch_set_wait_limit(self._h, int(ns)), "sco_batch_set_wait_limit")
 
     def autotune(self, trial_steps=2):
         t = BatchTuning()

@@ -117,6 +117,7 @@ struct sco_ctx {
   uint32_t g = 1;
   uint64_t nnz = 0;
   int sticky = 0;
+  unsigned long long ns_limit = 2000000000ull;  // bound of every device-side wait (2 s)
   // phase timing
   bool timing = false;
   struct Ev {
@@ -260,8 +261,8 @@ sco_status do_colour(sco_ctx* c) {
     SCO_TRY(cudaMalloc(&c->cb.scan_tmp, scan_tmp_bytes(tc > cap + 1 ? tc : cap + 1)));
     c->cls_cap = cap;
   }
-  SCO_TRY(kw_run(c->P, c->row_ptr, c->col, c->g, c->p.colour_variant, c->cb, c->cnt, c->st,
-                 &c->launches));
+  SCO_TRY(kw_run(c->P, c->row_ptr, c->col, c->g, c->p.colour_variant, c->cb, c->cnt,
+                 c->ns_limit, c->st, &c->launches));
   SCO_TRY(bucket_run(c->P, c->g, c->row_ptr, c->cb, c->cnt, c->st, &c->launches));
   c->colour_valid = true;
   return SCO_OK;
@@ -666,6 +667,13 @@ sco_status sco_get_timing(sco_ctx* c, double ms[3], int64_t calls[3]) {
 sco_status sco_sync(sco_ctx* c) {
   if (!c) return SCO_EINVAL;
   return read_counters(c);
+}
+
+sco_status sco_set_wait_limit(sco_ctx* c, uint64_t ns) {
+  if (!c || ns > 3600000000000ull) return SCO_EINVAL;
+  SCO_TRY(cudaStreamSynchronize(c->st));
+  c->ns_limit = ns;
+  return SCO_OK;
 }
 
 }  // extern "C"

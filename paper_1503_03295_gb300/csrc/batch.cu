@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256, 4) kb_kw_level(const BatchDev B, unsigned
         __nanosleep(nap);
         nap = nap < 2048 ? 2 * nap : 2048;
       }
-      if ((pass & 15) == 15 &&
+      if ((pass & wait_pass_mask(B.ns_limit)) == wait_pass_mask(B.ns_limit) &&
           (global_ns() - t_start > B.ns_limit || ld_status(&B.ctl->status) != 0)) {
         atomicCAS(&B.ctl->status, 0, kStatusTimeout);
         break;
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256, 4) kb_kw_level(const BatchDev B, unsigned
         __nanosleep(nap);
         nap = nap < 2048 ? 2 * nap : 2048;
       }
-      if ((pass & 15) == 15 &&
+      if ((pass & wait_pass_mask(B.ns_limit)) == wait_pass_mask(B.ns_limit) &&
           (global_ns() - t_start > B.ns_limit || ld_status(&B.ctl->status) != 0)) {
         atomicCAS(&B.ctl->status, 0, kStatusTimeout);
         break;

@@ -709,4 +709,12 @@ sco_status sco_batch_sync(sco_batch* b) {
   return read_ctl(b);
 }
 
+sco_status sco_batch_set_wait_limit(sco_batch* b, uint64_t ns) {
+  if (!b || ns > 3600000000000ull) return SCO_EINVAL;
+  SCO_TRY(cudaStreamSynchronize(b->st));
+  b->B.ns_limit = ns;
+  drop_graphs(b);  // captured launches hold the old limit
+  return SCO_OK;
+}
+
 }  // extern "C"

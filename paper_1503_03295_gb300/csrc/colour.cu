@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256, 4) k_kw_level(uint32_t N, uint32_t g, uns
         __nanosleep(nap);
         nap = nap < 2048 ? 2 * nap : 2048;
       }
-      if ((pass & 15) == 15 &&
+      if ((pass & wait_pass_mask(ns_limit)) == wait_pass_mask(ns_limit) &&
           (global_ns() - t_start > ns_limit || ld_status(&cnt->status) != 0)) {
         // bounded wait: give up (SCO_ETIMEOUT) after ns_limit or once another thread failed
         atomicCAS(&cnt->status, 0, kStatusTimeout);
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, 4) k_kw_level(uint32_t N, uint32_t g, uns
         __nanosleep(nap);
         nap = nap < 2048 ? 2 * nap : 2048;
       }
-      if ((pass & 15) == 15 &&
+      if ((pass & wait_pass_mask(ns_limit)) == wait_pass_mask(ns_limit) &&
           (global_ns() - t_start > ns_limit || ld_status(&cnt->status) != 0)) {
         atomicCAS(&cnt->status, 0, kStatusTimeout);
         break;
@@ -146,7 +146,13 @@ __global__ void k_kw_final(int64_t N, unsigned levels, uint32_t g, int variant,
                            const unsigned long long* __restrict__ word,
                            uint32_t* __restrict__ colour, DevCounters* __restrict__ cnt) {
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (v < N) colour[v] = (uint32_t)(word[v] & kColMask);
+  if (v < N) {
+    // a completed colouring has every colour below g; after a wait that gave up (sticky
+    // SCO_ETIMEOUT) an unfinished vertex may still hold one in [g, 2g): keep it inside the
+    // palette so that the class construction and the sweeps stay in bounds
+    const uint32_t c = (uint32_t)(word[v] & kColMask);
+    colour[v] = c < g ? c : g - 1;
+  }
   if (v == 0) {
     unsigned t = 0;
     for (unsigned p = 1; p <= levels; ++p) t += cnt->lev_rounds[p & 31];
@@ -317,8 +323,8 @@ cudaError_t low_setup(uint32_t gcap, int* blocks_per_sm, uint32_t* ecap) {
 }  // namespace
 
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
-                   uint32_t g, int variant, ColourBufs& b, DevCounters* cnt, cudaStream_t st,
-                   int64_t* launches) {
+                   uint32_t g, int variant, ColourBufs& b, DevCounters* cnt,
+                   unsigned long long ns_limit, cudaStream_t st, int64_t* launches) {
   const int64_t N = P.N;
   const int64_t G = (N + g - 1) / g;
   unsigned M = 0;  // levels (N < 2^30 keeps every index below 2^32)
@@ -328,7 +334,6 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   const unsigned nb = (unsigned)((N + 255) / 256);
   k_kw_init<<<nb, 256, 0, st>>>(N, g, b.word, b.col8, b.blk);
   ++*launches;
-  const unsigned long long ns_limit = 2000000000ull;  // 2 s per wait
   unsigned long long magic = div_magic(g);
   uint32_t* site_start = reinterpret_cast<uint32_t*>(b.meta);
   RepPlan* plan = reinterpret_cast<RepPlan*>(b.meta + 2);

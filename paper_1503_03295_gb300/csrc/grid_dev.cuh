@@ -55,7 +55,7 @@ __device__ __noinline__ bool grid_sync(unsigned* bar, int* status, unsigned long
       unsigned spins = 0;
       while (((ld_acquire_u32(&bar[0]) ^ old) & 0x80000000u) == 0) {
         __nanosleep(20);
-        if ((++spins & 255) == 0 && (global_ns() - t0 > ns_limit || ld_status(status) != 0)) {
+        if ((++spins & wait_spin_mask(ns_limit)) == 0 && (global_ns() - t0 > ns_limit || ld_status(status) != 0)) {
           atomicCAS(status, 0, kStatusTimeout);
           ok = 0;
           break;
@@ -93,7 +93,7 @@ __device__ __noinline__ bool grid_wait(unsigned* bar, const unsigned* s_old, int
       unsigned spins = 0;
       while (((ld_acquire_u32(&bar[0]) ^ old) & 0x80000000u) == 0) {
         __nanosleep(20);
-        if ((++spins & 255) == 0 && (global_ns() - t0 > ns_limit || ld_status(status) != 0)) {
+        if ((++spins & wait_spin_mask(ns_limit)) == 0 && (global_ns() - t0 > ns_limit || ld_status(status) != 0)) {
           atomicCAS(status, 0, kStatusTimeout);
           ok = 0;
           break;

@@ -155,7 +155,7 @@ __device__ __forceinline__ bool kw_item_recolour(const KwItem& it, const KwView&
       while (tag_of(wu) != p) {
         __nanosleep(64);
         wu = ld_relaxed(&V.word[u[a]]);
-        if ((++spins & 255) == 0 &&
+        if ((++spins & wait_spin_mask(V.ns_limit)) == 0 &&
             (global_ns() - t_start > V.ns_limit || ld_status(V.status) != 0)) {
           atomicCAS(V.status, 0, kStatusTimeout);
           return false;
@@ -234,7 +234,7 @@ __device__ __forceinline__ bool kw_recolour(uint32_t v, uint32_t c, const KwRow&
         while (tag_of(wu) != p) {
           __nanosleep(64);
           wu = ld_relaxed(&word[lo + uu[a]]);
-          if ((++spins & 255) == 0 &&
+          if ((++spins & wait_spin_mask(ns_limit)) == 0 &&
               (global_ns() - t_start > ns_limit || ld_status(status) != 0)) {
             atomicCAS(status, 0, kStatusTimeout);
             return false;

@@ -58,6 +58,17 @@ __device__ __forceinline__ int ld_status(const int* p) {
   return v;
 }
 
+// How often a bounded wait reads the clock: every 256th spin (every 16th pass) for the normal
+// limits of seconds, every spin (pass) for limits below 1 ms, so that a short limit is honoured
+// within one spin.  Returns the mask tested against the spin (or pass) counter.
+constexpr unsigned long long kShortWaitNs = 1000000ull;
+__device__ __forceinline__ unsigned wait_spin_mask(unsigned long long ns_limit) {
+  return ns_limit < kShortWaitNs ? 0u : 255u;
+}
+__device__ __forceinline__ unsigned wait_pass_mask(unsigned long long ns_limit) {
+  return ns_limit < kShortWaitNs ? 0u : 15u;
+}
+
 // floor(u / g) through the multiplier of g (see div_by_magic).
 __device__ __forceinline__ uint32_t fdiv(uint32_t u, unsigned long long M) {
   return div_by_magic(u, M);

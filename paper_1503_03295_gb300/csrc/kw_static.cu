@@ -130,9 +130,11 @@ __global__ void __launch_bounds__(256) k_st_level(uint32_t n, unsigned p,
   const uint32_t nth = gridDim.x * blockDim.x;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned rmax = 0;
+  unsigned nap = 64;  // back-off (ns) after a pass in which none of this thread's vertices moved
   bool pending = true;
   for (unsigned long long pass = 0; pending; ++pass) {
     pending = false;
+    bool progress = false;
     for (uint32_t r = tid; r < R; r += nth) {
       const uint32_t k = fdiv(r, M) >> (p - 1);
       const uint32_t v = (2 * k + 1) * half + (r - k * half);
@@ -179,6 +181,15 @@ __global__ void __launch_bounds__(256) k_st_level(uint32_t n, unsigned p,
       }
       rmax = max(rmax, rv + 1);
       st_relaxed(&word[v], pack(p, rv + 1, c));
+      progress = true;
+    }
+    if (pending) {
+      if (progress) {
+        nap = 64;
+      } else {
+        __nanosleep(nap);
+        nap = nap < 2048 ? 2 * nap : 2048;
+      }
     }
     if (pending && ((pass & 15) == 15) &&
         (global_ns() - t_start > ns_limit || ld_status(&ctrl->status) != 0)) {

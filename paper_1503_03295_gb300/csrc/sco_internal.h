@@ -111,9 +111,10 @@ struct ColourBufs {
 };
 constexpr uint32_t kMaxStablePalette = 12288;  // palettes up to this size get stable classes
 constexpr int64_t kClassTileSites = 2048;
+// ns_limit: bound of every device-side wait of the colouring kernels (SCO_ETIMEOUT after it)
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
-                   uint32_t g, int variant, ColourBufs& b, DevCounters* cnt, cudaStream_t st,
-                   int64_t* launches);
+                   uint32_t g, int variant, ColourBufs& b, DevCounters* cnt,
+                   unsigned long long ns_limit, cudaStream_t st, int64_t* launches);
 cudaError_t bucket_run(const DevParams& P, uint32_t g, const uint32_t* row_ptr, ColourBufs& b,
                        DevCounters* cnt, cudaStream_t st, int64_t* launches);
 

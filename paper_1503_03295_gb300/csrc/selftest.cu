@@ -118,10 +118,87 @@ sco_status run_test(int which, int64_t n, uint64_t seed, double* err, double* di
   return SCO_OK;
 }
 
+// ---- FP64 throughput probe ------------------------------------------------------------
+// Every thread advances kChains independent chains; a chain step is one FP64 FMA (kind 0),
+// one expm1_np6 evaluation plus one FMA (kind 1, arguments kept in [-0.43, -0.3]) or one
+// log_np evaluation plus one FMA (kind 2, arguments kept in [0.68, 0.75]).  The chains are
+// independent, so with every warp slot of every SM filled the FP64 pipe, not the latency of
+// one chain, bounds the rate.
+constexpr int kProbeChains = 8;
+
+template <int kKind>
+__global__ void __launch_bounds__(256) k_probe_fp64(int64_t iters, double a, double b,
+                                                    double* __restrict__ sink) {
+  double x[kProbeChains];
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c)
+    x[c] = (kKind == 2 ? 0.7 : -0.35) + 1e-6 * (double)((threadIdx.x + 37 * c) & 255);
+  for (int64_t k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) {
+      if (kKind == 0) x[c] = fma(x[c], a, b);
+      else if (kKind == 1) x[c] = fma(0.2, expm1_np_deg<6>(x[c]), -0.3);
+      else x[c] = fma(0.1, log_np(x[c]), 0.75);
+    }
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) acc += x[c];
+  if (acc == 1234.5) sink[0] = acc;  // never true: keeps the chains live
+}
+
+template <int kKind>
+cudaError_t probe_one(int64_t iters, double* per_s) {
+  int bps = 0, sms = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_probe_fp64<kKind>, 256, 0);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (bps < 1) bps = 1;
+  const unsigned grid = (unsigned)(bps * sms);
+  double* sink = nullptr;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  e = cudaMalloc(&sink, sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&ea);
+  if (e == cudaSuccess) e = cudaEventCreate(&eb);
+  if (e == cudaSuccess) {
+    // warm-up launch (clocks, instruction cache), then the timed one
+    k_probe_fp64<kKind><<<grid, 256>>>(iters / 8 + 1, 0.9999999, 1e-9, sink);
+    e = cudaEventRecord(ea);
+  }
+  if (e == cudaSuccess) {
+    k_probe_fp64<kKind><<<grid, 256>>>(iters, 0.9999999, 1e-9, sink);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(eb);
+  if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
+  if (e == cudaSuccess)
+    *per_s = (double)grid * 256.0 * (double)iters * kProbeChains / (ms * 1e-3);
+  if (ea) cudaEventDestroy(ea);
+  if (eb) cudaEventDestroy(eb);
+  cudaFree(sink);
+  return e;
+}
+
 }  // namespace
 }  // namespace sco
 
 using namespace sco;
+
+extern "C" sco_status sco_probe_fp64(int64_t iters, double out[3]) {
+  if (iters < 1 || iters > (1ll << 30) || !out) return SCO_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SCO_ECUDA;
+  if (probe_one<0>(iters, &out[0]) != cudaSuccess) return SCO_ECUDA;
+  // the elementary functions cost about a dozen FMAs each: fewer steps for the same time
+  const int64_t it2 = iters / 12 > 0 ? iters / 12 : 1;
+  if (probe_one<1>(it2, &out[1]) != cudaSuccess) return SCO_ECUDA;
+  if (probe_one<2>(it2, &out[2]) != cudaSuccess) return SCO_ECUDA;
+  return SCO_OK;
+}
 
 extern "C" sco_status sco_selftest_expm1_deg(int64_t n, uint64_t seed, int32_t degree,
                                              double* max_rel_err, double* max_rel_diff_cuda) {

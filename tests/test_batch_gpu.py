@@ -173,7 +173,15 @@ def test_batched_workload_64_replicas():
             lat = _single(ps[r], n)
             _same_replica(b, r, lat, n)
             lat.close()
-        p = ps[3]
-        o = O.Chain(O.make_params(p.Lx, p.Ly, T=p.T, J=p.J, D=p.D, seed=p.seed))
-        o.sweep(n)
-        assert np.array_equal(b.spins(3), o.spins())
+        # against the oracle directly: a small replica, and both ends of the largest size
+        # (replica 48: L = 512 at T = 0.2 D, mean degree about 37, the most work per site;
+        # replica 63: L = 512 at T = 1.5 D): spins, accept bits of the last step, colours, t_R
+        for r in (3, 48, 63):
+            p = ps[r]
+            o = O.Chain(O.make_params(p.Lx, p.Ly, T=p.T, J=p.J, D=p.D, seed=p.seed))
+            o.sweep(n)
+            assert np.array_equal(b.spins(r), o.spins()), r
+            assert np.array_equal(b.accepts(r), o.accepts()), r
+            assert np.array_equal(b.colours(r).astype(np.int32), o.colours()), r
+            assert b.observables(r)["kw_rounds"] == o.observables()["kw_rounds"], r
+            o.close()

@@ -21,8 +21,10 @@ def test_reference_arm_line():
     assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 1
     assert line["higher_is_better"] is True and line["vs_baseline"] is None
     assert line["value"] > 0 and line["ms_per_step"] > 0
-    # the same workload as the GPU arm names, a bounded sample of it actually run
-    assert line["config"]["L"] == 2304 and "L=2304" in line["config"]["workload"]
+    # the config names the lattice actually run, a bounded sample of the GPU arm's workload
+    assert line["config"]["L"] == 32 and line["config"]["N"] == 32 * 32
+    assert line["config"]["workload"].startswith("L=32 ")
+    assert line["config"]["sample_of"] == {"L": 2304, "N": 2304 * 2304}
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
     assert "L=32" in cb["sample"]

@@ -108,12 +108,19 @@ def test_trajectory_bit_exact(L, T, J, n):
     assert og["sweeps_done"] == oo["sweeps_done"] == n
 
 
-@pytest.mark.parametrize("T,seed", [(0.3, 1), (0.6, 2), (1.2, 3)])
+@pytest.mark.parametrize("T", [0.3, 0.6, 1.2])
+@pytest.mark.parametrize("seed", [1, 2, 3])
 def test_l256_first_50_sweeps(T, seed):
+    """The L = 256 workload, every (T, seed) pair of it: accept bits and spins bit-exact after
+    sweeps 1, 10 and 50, energy within 1e-12 relative."""
     g, o = _pair(256, T=T, seed=seed)
-    g.sweep(50)
-    o.sweep(50)
-    assert np.array_equal(g.spins(), o.spins())
+    done = 0
+    for upto in (1, 10, 50):
+        g.sweep(upto - done)
+        o.sweep(upto - done)
+        done = upto
+        assert np.array_equal(g.accepts(), o.accepts()), upto
+        assert np.array_equal(g.spins(), o.spins()), upto
     _same_energy(g.observables()["e_switched"], o.observables()["e_switched"], g.N)
 
 

@@ -47,6 +47,48 @@ def test_static_colouring_matches_sco_colour_on_consecutive_calls():
             assert delta == obs["max_degree"] and rounds == obs["kw_rounds"]
 
 
+def test_static_colouring_matches_the_oracle():
+    # The same graphs coloured by the oracle's KW (Sec. 2.3.3), which runs the literal
+    # synchronous rounds: colours and t_R must agree bit for bit.
+    import oracle as O
+    import torch
+
+    stream = torch.cuda.current_stream().cuda_stream
+    for L, T, seed, J, D, variant in [(64, 0.3, 5, 0.0, 1.0, 0), (48, 0.9, 6, 1.0, 0.1, 1)]:
+        rp, col, _, _ = _reference(L, T, seed, J, D, variant)
+        ref, ref_rounds, ref_delta = O.kw_colour_graph(rp.astype(np.int64), col, variant)
+        n = L * L
+        d_rp = torch.from_numpy(rp.view(np.int32).copy()).cuda()
+        d_col = torch.from_numpy(col.view(np.int32).copy()).cuda()
+        out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        delta, rounds = sco.kw_colour_static(d_rp.data_ptr(), d_col.data_ptr(), n,
+                                             out.data_ptr(), variant=variant, stream=stream)
+        assert np.array_equal(out.cpu().numpy(), ref)
+        assert delta == ref_delta and rounds == ref_rounds
+
+
+def test_static_colouring_at_its_maximum_size():
+    # n = SCO_KW_STATIC_MAX_VERTICES exactly (an L = 1024 lattice at T = 0.4 D), where the
+    # context path colours the upper KW levels with its bucketed kernel: same colours, max
+    # degree and t_R, and no bounded wait runs out, on two calls in a row.
+    import torch
+
+    L = 1024
+    assert L * L == sco.KW_STATIC_MAX_VERTICES
+    stream = torch.cuda.current_stream().cuda_stream
+    rp, col, ref, obs = _reference(L, 0.4, 1)
+    n = L * L
+    d_rp = torch.from_numpy(rp.view(np.int32).copy()).cuda()
+    d_col = torch.from_numpy(col.view(np.int32).copy()).cuda()
+    out = torch.empty((n,), dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        out.fill_(-1)
+        delta, rounds = sco.kw_colour_static(d_rp.data_ptr(), d_col.data_ptr(), n,
+                                             out.data_ptr(), variant=0, stream=stream)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
+        assert delta == obs["max_degree"] and rounds == obs["kw_rounds"]
+
+
 def test_static_colouring_rejects_oversize_without_device_work():
     lib = sco.load()
     d, r = C.c_int32(-7), C.c_int32(-7)
