@@ -134,6 +134,40 @@ sco_status sco_get_accepts(sco_ctx* c, uint8_t* acc);
 sco_status sco_get_table(sco_ctx* c, int64_t* K, int32_t* dx, int32_t* dy, uint64_t* W,
                          double* cc);
 
+/* Changes the temperature (the cooling protocol of Sec. 3.1 lowers T step by step and carries
+ * the spins over): rebuilds the temperature-dependent tables and drops the switched graph,
+ * which belonged to the old T; the next MC step switches and colours again (same epoch
+ * number, so the random streams stay those of a lattice started at the new T from the same
+ * spins and step).  T > 0 and finite, else SCO_EINVAL.  Synchronises. */
+sco_status sco_set_temperature(sco_ctx* c, double T);
+
+/* Graph diagnostics of the current switched graph and its colouring, computed on the device:
+ *  - P_survive(r) (Sec. 3.2, Fig. 5): per distance shell, surviving dipolar pairs over all
+ *    site pairs of the open lattice in it; bin b holds b + 1 <= r < b + 2, the last of the
+ *    n_rbins bins (1 <= n_rbins <= 4096) everything beyond;
+ *  - P_IPC (Sec. 3.2, Fig. 6): the fraction of surviving dipolar pairs whose two sites lie in
+ *    different cells of a virtual cells_x x cells_y split of the lattice into rectangles, site
+ *    (x, y) in cell (floor(x cells_x / Lx), floor(y cells_y / Ly)) (1 <= cells_x <= Lx,
+ *    1 <= cells_y <= Ly, palette x cells <= 2^28);
+ *  - Delta R (Sec. 3.3, Eq. (9)) per colour: (K_max - K_ave) / K_ave, K the number of sites of
+ *    that colour in a cell and K_ave the class size over the number of cells (NaN for an empty
+ *    colour), with its mean and maximum over the non-empty colours.
+ * survived and pairs (int64, n_rbins), p_survive (n_rbins) and delta_r (palette = Delta + 1
+ * entries) are host buffers; any may be NULL.  SCO_ESTATE before the first colouring.
+ * Synchronises; allocates its device scratch for the call. */
+typedef struct {
+  int64_t n_pairs;     /* surviving dipolar pairs */
+  int64_t n_cross;     /* of which the two sites lie in different cells */
+  double p_ipc;        /* n_cross / n_pairs (0 without pairs) */
+  double delta_r_mean; /* mean of Eq. (9) over the non-empty colours */
+  double delta_r_max;  /* its maximum */
+  int32_t n_cells;     /* cells_x * cells_y */
+  int32_t palette;     /* Delta + 1 */
+} sco_graph_stats;
+sco_status sco_get_graph_stats(sco_ctx* c, int32_t cells_x, int32_t cells_y, int32_t n_rbins,
+                               sco_graph_stats* out, int64_t* survived, int64_t* pairs,
+                               double* p_survive, double* delta_r);
+
 /* Checkpoint: a byte blob holding the parameters, the step counter, the spins and (when the
  * current epoch started before the current step) the spins at the epoch start, from which
  * the epoch's graph is rebuilt.  sco_get_state with buf == NULL returns the size in *len.

@@ -34,6 +34,15 @@ class Obs(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GraphStats(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("n_cross", C.c_int64), ("p_ipc", C.c_double),
+                ("delta_r_mean", C.c_double), ("delta_r_max", C.c_double),
+                ("n_cells", C.c_int32), ("palette", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _P = np.ctypeslib.ndpointer
 
@@ -84,6 +93,9 @@ def lib():
         L.sco_ref_plain_metropolis.argtypes = [C.POINTER(Params), vp, C.c_int64, vp, vp, vp]
         L.sco_ref_full_energy.argtypes = [C.POINTER(Params), vp]
         L.sco_ref_full_energy.restype = C.c_double
+        L.sco_ref_set_temperature.argtypes = [vp, C.c_double]
+        L.sco_ref_graph_stats.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32,
+                                          C.POINTER(GraphStats), vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -275,6 +287,27 @@ class Chain:
         s = np.zeros(self.N * self.N, np.uint8)
         _check(lib().sco_ref_direct_switch(self._h, epoch, _ptr(s)), "direct_switch")
         return s.reshape(self.N, self.N)
+
+    def set_temperature(self, T):
+        _check(lib().sco_ref_set_temperature(self._h, float(T)), "set_temperature")
+        self.params.T = float(T)
+
+    def graph_stats(self, cells_x=1, cells_y=1, n_rbins=64):
+        """P_survive per distance shell, P_IPC and Delta R (see sco_ref_graph_stats)."""
+        st = GraphStats()
+        surv = np.zeros(n_rbins, np.int64)
+        pairs = np.zeros(n_rbins, np.int64)
+        ps = np.zeros(n_rbins)
+        pal = int(self.colours().max()) + 1 if self.N else 1
+        rp, _ = self.graph()
+        delta = int(np.max(np.diff(rp))) if self.N else 0
+        dr = np.zeros(max(pal, delta + 1))
+        _check(lib().sco_ref_graph_stats(self._h, cells_x, cells_y, n_rbins, C.byref(st),
+                                         _ptr(surv), _ptr(pairs), _ptr(ps), _ptr(dr)),
+               "graph_stats")
+        out = st.as_dict()
+        out.update(survived=surv, pairs=pairs, p_survive=ps, delta_r=dr[:st.palette])
+        return out
 
     @property
     def sweeps_done(self):

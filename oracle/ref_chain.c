@@ -877,3 +877,113 @@ int sco_ref_run_series(sco_ref_ctx* c, int64_t n_mcs, double* e_per_spin, double
   }
   return SCO_REF_OK;
 }
+
+/* ---- temperature (the cooling protocol of Sec. 3.1) ------------------------------------ */
+int sco_ref_set_temperature(sco_ref_ctx* c, double T) {
+  if (!c || !(T > 0.0) || !isfinite(T)) return SCO_REF_EINVAL;
+  c->p.T = T;
+  c->beta = 1.0 / T;
+  c->bD = c->beta * c->p.D;
+  /* the switched graph belongs to the old temperature: switch (and colour) again before the
+     next MC step, at the same epoch number */
+  c->graph_epoch = -1;
+  c->colour_valid = 0;
+  return SCO_REF_OK;
+}
+
+/* ---- graph diagnostics (Sec. 3.2, Figs. 5 and 6; Sec. 3.3, Eq. (9)) -------------------- */
+/* floor(sqrt(r2)) exactly: the rounded root corrected by integer comparisons */
+static int64_t floor_sqrt(int64_t r2) {
+  int64_t s = (int64_t)sqrt((double)r2);
+  while (s * s > r2) --s;
+  while ((s + 1) * (s + 1) <= r2) ++s;
+  return s;
+}
+
+/* distance shell of a pair: bin b holds b + 1 <= r < b + 2, the last bin everything beyond */
+static int32_t shell_bin(int64_t r2, int32_t n_rbins) {
+  const int64_t b = floor_sqrt(r2) - 1;
+  return (int32_t)(b < n_rbins - 1 ? b : n_rbins - 1);
+}
+
+/* cell of site (x, y) in a cells_x x cells_y split of the lattice into rectangles */
+static int64_t cell_of(const sco_ref_params* p, int64_t i, int32_t cx, int32_t cy) {
+  const int64_t x = i % p->Lx, y = i / p->Lx;
+  return (x * cx) / p->Lx + (int64_t)cx * ((y * cy) / p->Ly);
+}
+
+int sco_ref_graph_stats(const sco_ref_ctx* c, int32_t cells_x, int32_t cells_y, int32_t n_rbins,
+                        sco_ref_gstats* out, int64_t* survived, int64_t* pairs,
+                        double* p_survive, double* delta_r) {
+  if (!c || !out || cells_x < 1 || cells_y < 1 || cells_x > c->p.Lx || cells_y > c->p.Ly ||
+      n_rbins < 1)
+    return SCO_REF_EINVAL;
+  if (c->graph_epoch < 0 || !c->colour_valid) return SCO_REF_EINVAL;
+  const int32_t Lx = c->p.Lx, Ly = c->p.Ly;
+  const int64_t ncell = (int64_t)cells_x * cells_y;
+  int64_t* surv = (int64_t*)calloc((size_t)n_rbins, sizeof(int64_t));
+  int64_t* npair = (int64_t*)calloc((size_t)n_rbins, sizeof(int64_t));
+  int64_t* K = (int64_t*)calloc((size_t)(ncell * c->g), sizeof(int64_t));
+  if (!surv || !npair || !K) {
+    free(surv);
+    free(npair);
+    free(K);
+    return SCO_REF_ENOMEM;
+  }
+  /* every pair of the open lattice once: displacement d of the half plane, (Lx-|dx|)(Ly-|dy|)
+     site pairs (i, i + d) inside the lattice */
+  for (int64_t m = 0; m < c->K; ++m) {
+    const int64_t ax = c->tdx[m] < 0 ? -c->tdx[m] : c->tdx[m];
+    const int64_t ay = c->tdy[m];
+    npair[shell_bin(c->tr2[m], n_rbins)] += (Lx - ax) * (Ly - ay);
+  }
+  /* surviving dipolar pairs by shell, and those whose sites lie in different cells (P_IPC) */
+  int64_t ndip = 0, ncross = 0;
+  for (int64_t q = 0; q < c->ne; ++q) {
+    if (!(c->ef[q] & 1)) continue;
+    const int64_t i = c->ei[q], j = c->ej[q];
+    const int64_t dx = j % Lx - i % Lx, dy = j / Lx - i / Lx;
+    ++surv[shell_bin(dx * dx + dy * dy, n_rbins)];
+    ++ndip;
+    if (cell_of(&c->p, i, cells_x, cells_y) != cell_of(&c->p, j, cells_x, cells_y)) ++ncross;
+  }
+  /* sites of each colour in each cell; Eq. (9) per colour: (K_max - K_ave) / K_ave with K_ave
+     the class size over the number of cells */
+  for (int64_t i = 0; i < c->N; ++i)
+    ++K[(int64_t)c->colour[i] * ncell + cell_of(&c->p, i, cells_x, cells_y)];
+  double sum = 0.0, dmax = 0.0;
+  int32_t nonempty = 0;
+  for (int32_t col = 0; col < c->g; ++col) {
+    int64_t tot = 0, kmax = 0;
+    for (int64_t q = 0; q < ncell; ++q) {
+      const int64_t k = K[(int64_t)col * ncell + q];
+      tot += k;
+      if (k > kmax) kmax = k;
+    }
+    double dr = NAN;
+    if (tot > 0) {
+      const double kave = (double)tot / (double)ncell;
+      dr = ((double)kmax - kave) / kave;
+      sum += dr;
+      if (dr > dmax) dmax = dr;
+      ++nonempty;
+    }
+    if (delta_r) delta_r[col] = dr;
+  }
+  for (int32_t b = 0; b < n_rbins; ++b) {
+    if (survived) survived[b] = surv[b];
+    if (pairs) pairs[b] = npair[b];
+    if (p_survive) p_survive[b] = npair[b] > 0 ? (double)surv[b] / (double)npair[b] : NAN;
+  }
+  out->n_pairs = ndip;
+  out->n_cross = ncross;
+  out->p_ipc = ndip > 0 ? (double)ncross / (double)ndip : 0.0;
+  out->delta_r_mean = nonempty > 0 ? sum / nonempty : 0.0;
+  out->delta_r_max = dmax;
+  out->n_cells = (int32_t)ncell;
+  out->palette = c->g;
+  free(surv);
+  free(npair);
+  free(K);
+  return SCO_REF_OK;
+}

@@ -124,6 +124,35 @@ void sco_ref_set_threads(int32_t n); /* OpenMP threads (<= 0: library default) *
 /* Scale of every FP64 error bound (1 = normal; huge = always extended precision). */
 void sco_ref_set_guard_scale(double s);
 
+/* Changes T (the cooling protocol of Sec. 3.1: the paper lowers T in steps, carrying the spins
+ * over); the graph of the old T is dropped and the next MC step switches again at its epoch. */
+int sco_ref_set_temperature(sco_ref_ctx* c, double T);
+
+/* Graph diagnostics of the current switched graph and colouring.
+ *  - P_survive(r) (Sec. 3.2, Fig. 5): per distance shell (bin b: b+1 <= r < b+2, the last bin
+ *    open-ended), surviving dipolar pairs over all site pairs of the open lattice in it.
+ *  - P_IPC (Sec. 3.2, Fig. 6): the fraction of surviving dipolar pairs whose two sites lie in
+ *    different cells of a cells_x x cells_y split of the lattice (site (x, y) in cell
+ *    (floor(x cells_x / Lx), floor(y cells_y / Ly))).
+ *  - Delta R (Sec. 3.3, Eq. (9)) per colour: (K_max - K_ave) / K_ave over the cells, K the
+ *    number of sites of that colour in a cell (NaN for an empty colour); mean and max over the
+ *    non-empty colours.
+ * Any of survived, pairs, p_survive (n_rbins each) and delta_r (palette) may be NULL.
+ * Pinned by: brute-force pair counts, the closed-form survival probability for uniform spins,
+ * one-cell and one-site-per-cell limits, numpy recounts of the edge list and colours. */
+typedef struct {
+  int64_t n_pairs;     /* surviving dipolar pairs */
+  int64_t n_cross;     /* of which the two sites lie in different cells */
+  double p_ipc;        /* n_cross / n_pairs (0 without pairs) */
+  double delta_r_mean; /* mean of Eq. (9) over the non-empty colours */
+  double delta_r_max;
+  int32_t n_cells;
+  int32_t palette;
+} sco_ref_gstats;
+int sco_ref_graph_stats(const sco_ref_ctx* c, int32_t cells_x, int32_t cells_y, int32_t n_rbins,
+                        sco_ref_gstats* out, int64_t* survived, int64_t* pairs,
+                        double* p_survive, double* delta_r);
+
 /* KW colouring (Sec. 2.3.3) of an arbitrary symmetric CSR graph; bit 31 of col is ignored.
  * Pinned by: validity, palette [0, Delta], t_R <= (Delta+1)M (Eq. (5)), brute force. */
 int sco_ref_kw_colour_graph(int64_t N, const int64_t* row_ptr, const uint32_t* col,

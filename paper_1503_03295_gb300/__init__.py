@@ -55,6 +55,15 @@ class Obs(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GraphStats(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("n_cross", C.c_int64), ("p_ipc", C.c_double),
+                ("delta_r_mean", C.c_double), ("delta_r_max", C.c_double),
+                ("n_cells", C.c_int32), ("palette", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -89,6 +98,9 @@ def load():
         "sco_get_timing": ([vp, vp, vp], st),
         "sco_sync": ([vp], st),
         "sco_set_wait_limit": ([vp, C.c_uint64], st),
+        "sco_set_temperature": ([vp, C.c_double], st),
+        "sco_get_graph_stats": ([vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(GraphStats),
+                                 vp, vp, vp, vp], st),
         "sco_batch_set_wait_limit": ([vp, C.c_uint64], st),
         "sco_kw_colour_static": ([vp, vp, C.c_int64, C.c_int32, vp, C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], st),
@@ -243,6 +255,27 @@ class Lattice:
     def set_wait_limit(self, ns):
         """Bound (ns) of every device-side wait (see sco_set_wait_limit)."""
         _check(load().sco_set_wait_limit(self._h, int(ns)), "sco_set_wait_limit")
+
+    def set_temperature(self, T):
+        """New temperature; the next MC step switches again (see sco_set_temperature)."""
+        _check(load().sco_set_temperature(self._h, float(T)), "sco_set_temperature")
+        self.params.T = float(T)
+
+    def graph_stats(self, cells_x=1, cells_y=1, n_rbins=64):
+        """P_survive per distance shell, P_IPC of a cells_x x cells_y split and Delta R per
+        colour of the current graph (see sco_get_graph_stats)."""
+        _, _, _, g = self.sizes()
+        st = GraphStats()
+        surv = np.zeros(n_rbins, np.int64)
+        pairs = np.zeros(n_rbins, np.int64)
+        ps = np.zeros(n_rbins)
+        dr = np.zeros(max(g, 1))
+        _check(load().sco_get_graph_stats(self._h, int(cells_x), int(cells_y), int(n_rbins),
+                                          C.byref(st), _ptr(surv), _ptr(pairs), _ptr(ps),
+                                          _ptr(dr)), "sco_get_graph_stats")
+        out = st.as_dict()
+        out.update(survived=surv, pairs=pairs, p_survive=ps, delta_r=dr[:st.palette])
+        return out
 
     # ---- data -----------------------------------------------------------------------
     def spins(self):

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libsco.so")
 SOURCES = ["api.cu", "scan.cu", "table.cu", "spins.cu", "switch.cu", "colour.cu", "sweep.cu",
-           "kw_static.cu", "batch.cu", "batch_api.cu", "selftest.cu"]
+           "kw_static.cu", "batch.cu", "batch_api.cu", "selftest.cu", "stats.cu"]
 HEADERS = ["sco_device.cuh", "sco_internal.h", "switch_dev.cuh", "sweep_dev.cuh", "kw_dev.cuh", "batch.h", "grid_dev.cuh", "kw_bcr.cuh", "kw_low.cuh", "expm1_poly.h", "log_table.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -669,6 +669,56 @@ sco_status sco_sync(sco_ctx* c) {
   return read_counters(c);
 }
 
+sco_status sco_set_temperature(sco_ctx* c, double T) {
+  if (!c) return SCO_EINVAL;
+  if (c->sticky) return (sco_status)c->sticky;
+  sco_params q = c->p;
+  q.T = T;
+  if (!params_ok(&q)) return SCO_EINVAL;
+  SCO_TRY(cudaStreamSynchronize(c->st));
+  c->p = q;
+  c->P = make_dev_params(q);
+  // the temperature-dependent tables (pair energies scaled by beta, candidate probabilities)
+  table_free_xy(c->tab);
+  SCO_TRY(table_build_xy(c->P, c->tab, c->st, &c->launches));
+  SCO_TRY(cudaStreamSynchronize(c->st));
+  // the graph belongs to the old temperature: the next MC step switches again, same epoch
+  c->graph_epoch = -1;
+  c->colour_valid = false;
+  return SCO_OK;
+}
+
+sco_status sco_get_graph_stats(sco_ctx* c, int32_t cells_x, int32_t cells_y, int32_t n_rbins,
+                               sco_graph_stats* out, int64_t* survived, int64_t* pairs,
+                               double* p_survive, double* delta_r) {
+  if (!c || !out || cells_x < 1 || cells_y < 1 || cells_x > c->p.Lx || cells_y > c->p.Ly ||
+      n_rbins < 1 || n_rbins > 4096)
+    return SCO_EINVAL;
+  if ((uint64_t)c->g * (uint64_t)cells_x * (uint64_t)cells_y > (1ull << 28)) return SCO_EINVAL;
+  if (c->sticky) return (sco_status)c->sticky;
+  if (c->graph_epoch < 0 || !c->colour_valid) return SCO_ESTATE;
+  const size_t nb = (size_t)n_rbins;
+  std::vector<unsigned long long> cnt(2 * nb + 1);
+  std::vector<double> fo(5 + (size_t)c->g + nb);
+  SCO_TRY(graph_stats_run(c->P, c->tab.disp, c->row_ptr, c->col, c->cb.colour, c->g, cells_x,
+                          cells_y, n_rbins, c->st, &c->launches, cnt.data(), fo.data()));
+  out->n_pairs = (int64_t)fo[0];
+  out->n_cross = (int64_t)cnt[2 * nb];
+  out->p_ipc = fo[2];
+  out->delta_r_mean = fo[3];
+  out->delta_r_max = fo[4];
+  out->n_cells = cells_x * cells_y;
+  out->palette = (int32_t)c->g;
+  for (size_t b = 0; b < nb; ++b) {
+    if (survived) survived[b] = (int64_t)cnt[b];
+    if (pairs) pairs[b] = (int64_t)cnt[nb + b];
+    if (p_survive) p_survive[b] = fo[5 + c->g + b];
+  }
+  if (delta_r)
+    for (uint32_t k = 0; k < c->g; ++k) delta_r[k] = fo[5 + k];
+  return read_counters(c);
+}
+
 sco_status sco_set_wait_limit(sco_ctx* c, uint64_t ns) {
   if (!c || ns > 3600000000000ull) return SCO_EINVAL;
   SCO_TRY(cudaStreamSynchronize(c->st));

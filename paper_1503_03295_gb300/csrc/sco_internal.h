@@ -125,6 +125,15 @@ cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32
                       uint8_t* acc, uint32_t* defer, uint32_t* dcnt, double4_32a* prop,
                       DevCounters* cnt, cudaStream_t st, int64_t* launches);
 
+// ---- stats.cu ----
+// Graph diagnostics (see sco_get_graph_stats); copies 2 nb + 1 counts (survived, pairs, cross)
+// to h_counts and 5 + g + nb doubles (summary, Delta R per colour, P_survive) to h_out, then
+// synchronises.
+cudaError_t graph_stats_run(const DevParams& P, const uint32_t* disp, const uint32_t* row_ptr,
+                            const uint32_t* col, const uint32_t* colour, uint32_t g, int cx,
+                            int cy, int nb, cudaStream_t st, int64_t* launches,
+                            unsigned long long* h_counts, double* h_out);
+
 int num_sms();
 
 }  // namespace sco
