@@ -66,6 +66,18 @@ def parse():
     ap.add_argument("--prec-L", type=int, default=1024)
     ap.add_argument("--no-kw-bound", action="store_true",
                     help="skip t_R of both colour-reduction variants against Eq. (5)'s bound")
+    ap.add_argument("--protocol", action="store_true",
+                    help="run the paper's cooling protocol instead (Table 1 at L=2304, M_phi(T) "
+                         "at L=128) and print its JSON line")
+    ap.add_argument("--proto-L", type=int, default=2304)
+    ap.add_argument("--proto-eq", type=int, default=1000,
+                    help="MC steps at every temperature of the L=2304 cooling")
+    ap.add_argument("--proto-graphs", type=int, default=35,
+                    help="graphs (epochs of n_sw steps) averaged at each Table 1 temperature")
+    ap.add_argument("--mphi-L", type=int, default=128)
+    ap.add_argument("--mphi-runs", type=int, default=10)
+    ap.add_argument("--mphi-eq", type=int, default=2000)
+    ap.add_argument("--mphi-meas", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -499,6 +511,119 @@ def run_batch(args, rank, local):
     }
 
 
+# Table 1 of the paper: T / J, <k>, <Delta> at L = 2304 over 35 graphs
+TABLE1 = {1.25: (1.40, 8.54), 0.45: (3.36, 12.9), 0.05: (22.7, 41.6)}
+# virtual cell splits of the L = 2304 lattice for the processor counts of Fig. 6: the factor
+# pair of N_proc closest to square (the paper's cells are squares where N_proc allows)
+CELL_SPLITS = {48: (6, 8), 144: (12, 12), 288: (16, 18)}
+
+
+def cooling_schedule(T_hi=1.25, T_lo=0.05, dT=0.05):
+    """Temperatures of Sec. 3.1's cooling, T_hi down to T_lo in steps of dT (in units of J)."""
+    n = int(round((T_hi - T_lo) / dT))
+    return [round(T_hi - k * dT, 10) for k in range(n + 1)]
+
+
+def _mean_sem(x):
+    import numpy as np
+
+    x = np.asarray(x, float)
+    return float(x.mean()), float(x.std(ddof=1) / np.sqrt(len(x))) if len(x) > 1 else 0.0
+
+
+def run_protocol(args, local):
+    """Sec. 3.1's protocol on the paper's model (J = 1, D = 0.1, n_sw = 100): cooling from 1.25 J
+    to 0.05 J in steps of 0.05 J with the spins carried over.  (1) L = 2304 (FP32-guarded, whose
+    decisions equal the FP64 form's): at the three temperatures of Table 1, <k> and <Delta> over
+    35 graphs, and the graph diagnostics of Figs. 5, 6 and Eq. (9); (2) L = 128, several
+    independent runs advanced together as a batch: |M_phi| of Eq. (7) against T."""
+    import numpy as np
+    import torch
+    import paper_1503_03295_gb300 as sco
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    n_sw = 100
+    sched = cooling_schedule()
+    t0 = time.perf_counter()
+    L = args.proto_L
+    N = L * L
+    lat = sco.Lattice(sco.make_params(L, T=sched[0], J=1.0, D=0.1, seed=args.seed, n_sw=n_sw,
+                                      precision=sco.FP32_GUARDED), stream=stream.cuda_stream)
+    rows = []
+    ms_mc = []
+    for T in sched:
+        lat.set_temperature(T)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            lat.sweep(args.proto_eq)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_mc.append(e0.elapsed_time(e1) / args.proto_eq)
+        key = min(TABLE1, key=lambda a: abs(a - T))
+        if abs(key - T) > 1e-9:
+            continue
+        ks, ds, dr, pipc, ps = [], [], [], {n: [] for n in CELL_SPLITS}, []
+        for _ in range(args.proto_graphs):
+            lat.sweep(n_sw)  # the epoch's graph is switched at its first step
+            o = lat.observables()
+            ks.append(2.0 * o["n_edges"] / N)
+            ds.append(o["max_degree_dipolar"])
+            for nproc, (cx, cy) in CELL_SPLITS.items():
+                st = lat.graph_stats(cx, cy, 64)
+                pipc[nproc].append(st["p_ipc"])
+                if nproc == 288:
+                    dr.append(st["delta_r_mean"])
+                    ps.append(st["p_survive"])
+        o = lat.observables()
+        k_m, k_s = _mean_sem(ks)
+        d_m, d_s = _mean_sem(ds)
+        pmean = np.mean(np.asarray(ps), axis=0)
+        rows.append({"T_J": T, "k_mean": k_m, "k_sem": k_s, "delta_mean": d_m, "delta_sem": d_s,
+                     "graphs": len(ks), "paper_k": TABLE1[key][0], "paper_delta": TABLE1[key][1],
+                     "m_phi": o["m_phi"], "m_abs": o["m_abs"],
+                     "e_switched_per_spin": o["e_switched"] / N,
+                     "p_survive_r1_to_r16": [float(x) for x in pmean[:16]],
+                     "p_ipc": {str(n): _mean_sem(v)[0] for n, v in pipc.items()},
+                     "delta_r_mean_288_cells": _mean_sem(dr)[0]})
+    lat.close()
+    t1 = time.perf_counter()
+    # (2) M_phi(T): independent runs (seeds 0..R-1) as one batch
+    R = args.mphi_runs
+    ps_ = [sco.make_params(args.mphi_L, T=sched[0], J=1.0, D=0.1, seed=s, n_sw=n_sw,
+                           precision=sco.FP32_GUARDED) for s in range(R)]
+    b = sco.Batch(ps_, stream=stream.cuda_stream)
+    curve = []
+    every = 10
+    for T in sched:
+        for r in range(R):
+            b.set_temperature(r, T)
+        b.run(args.mphi_eq)
+        acc = np.zeros(R)
+        nm = 0
+        for _ in range(args.mphi_meas // every):
+            b.run(every)
+            acc += [abs(b.observables(r)["m_phi"]) for r in range(R)]
+            nm += 1
+        m, sem = _mean_sem(acc / nm)
+        curve.append({"T_J": T, "m_phi_abs": m, "sem": sem})
+    b.close()
+    t2 = time.perf_counter()
+    return {
+        "protocol": "Sec. 3.1: J=1, D=0.1, n_sw=100, cooling 1.25J -> 0.05J in 0.05J steps",
+        "table1": {"L": L, "precision": "fp32_guarded", "steps_per_T": args.proto_eq,
+                   "graphs_per_T": args.proto_graphs, "rows": rows,
+                   "ms_per_mc_step_by_T": dict(zip([str(t) for t in sched], ms_mc)),
+                   "cell_splits": {str(k): v for k, v in CELL_SPLITS.items()},
+                   "wall_s": t1 - t0},
+        "m_phi": {"L": args.mphi_L, "runs": R, "eq_steps": args.mphi_eq,
+                  "meas_steps": args.mphi_meas, "every": every, "curve": curve,
+                  "wall_s": t2 - t1},
+    }
+
+
 def cpu_baseline(L, T, seed):
     import oracle as O
 
@@ -521,6 +646,10 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.protocol:
+        if rank == 0:
+            print(json.dumps(run_protocol(args, local)), flush=True)
+        return
     if args.only_batch:
         import torch
         torch.cuda.set_device(local)

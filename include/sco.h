@@ -279,6 +279,13 @@ sco_status sco_batch_info(sco_batch* b, int64_t* total_sites, int64_t* steps_don
 /* Waits for the batch's stream; returns the sticky device status. */
 sco_status sco_batch_sync(sco_batch* b);
 
+/* Changes replica r's temperature (the cooling protocol of Sec. 3.1, run for many replicas at
+ * once).  Allowed only between MC steps t with t mod n_sw = 0 (else SCO_ESTATE), where every
+ * replica switches again anyway, so the change takes effect with the next step's switch; the
+ * replica then follows the trajectory of a single lattice given the same sco_set_temperature
+ * calls at the same steps.  Drops the captured graphs.  Synchronises. */
+sco_status sco_batch_set_temperature(sco_batch* b, int32_t r, double T);
+
 /* The same bound for the batch's kernels (grid barriers of the persistent sweep and of the
  * colouring, neighbour waits); drops the captured graphs.  Synchronises. */
 sco_status sco_batch_set_wait_limit(sco_batch* b, uint64_t ns);

@@ -102,6 +102,7 @@ def load():
         "sco_get_graph_stats": ([vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(GraphStats),
                                  vp, vp, vp, vp], st),
         "sco_batch_set_wait_limit": ([vp, C.c_uint64], st),
+        "sco_batch_set_temperature": ([vp, C.c_int32, C.c_double], st),
         "sco_kw_colour_static": ([vp, vp, C.c_int64, C.c_int32, vp, C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), vp], st),
         "sco_strerror": ([C.c_int], C.c_char_p),
@@ -400,6 +401,13 @@ class Batch:
 
     def set_wait_limit(self, ns):
         _check(load().sco_batch_set_wait_limit(self._h, int(ns)), "sco_batch_set_wait_limit")
+
+    def set_temperature(self, r, T):
+        """Replica r's new temperature, between steps t with t mod n_sw = 0 (see
+        sco_batch_set_temperature)."""
+        _check(load().sco_batch_set_temperature(self._h, int(r), float(T)),
+               "sco_batch_set_temperature")
+        self.params[r].T = float(T)
 
     def autotune(self, trial_steps=2):
         t = BatchTuning()

@@ -709,6 +709,34 @@ sco_status sco_batch_sync(sco_batch* b) {
   return read_ctl(b);
 }
 
+sco_status sco_batch_set_temperature(sco_batch* b, int32_t r, double T) {
+  if (!b || r < 0 || r >= b->R) return SCO_EINVAL;
+  if (b->sticky) return (sco_status)b->sticky;
+  sco_params q = b->p[r];
+  q.T = T;
+  if (!params_ok(&q)) return SCO_EINVAL;
+  // every replica switches at the steps t with t mod n_sw = 0: a change there takes effect with
+  // that switch, so the replica's graph never mixes two temperatures
+  if (b->t % b->B.n_sw != 0) return SCO_ESTATE;
+  SCO_TRY(cudaStreamSynchronize(b->st));
+  drop_graphs(b);
+  b->p[r] = q;
+  b->P[r] = make_dev_params(q);
+  table_free_xy(b->xy[r]);
+  SCO_TRY(table_build_xy(b->P[r], b->xy[r], b->st, &b->launches));
+  RepDesc& d = b->desc[r];
+  d.P = b->P[r];
+  d.xy = b->xy[r].xy;
+  d.xyq = b->xy[r].xyq;
+  d.xy32 = b->xy[r].xy32;
+  d.sw64 = b->xy[r].sw64;
+  d.sw32 = b->xy[r].sw32;
+  SCO_TRY(cudaMemcpyAsync(const_cast<RepDesc*>(b->B.desc) + r, &d, sizeof(RepDesc),
+                          cudaMemcpyHostToDevice, b->st));
+  SCO_TRY(cudaStreamSynchronize(b->st));
+  return SCO_OK;
+}
+
 sco_status sco_batch_set_wait_limit(sco_batch* b, uint64_t ns) {
   if (!b || ns > 3600000000000ull) return SCO_EINVAL;
   SCO_TRY(cudaStreamSynchronize(b->st));

@@ -55,3 +55,13 @@ def test_algorithmic_work_figures():
     f = bench.algorithmic_flops(k, 14.4)
     assert f["colour"] == 0.0
     assert abs(f["switch"] - 70 * 14.4) < 1e-9 and abs(f["sweep"] - 120 * k) < 1e-9
+
+
+def test_cooling_schedule_and_cell_splits():
+    # Sec. 3.1: from 1.25 J down to 0.05 J in steps of 0.05 J (25 temperatures)
+    s = bench.cooling_schedule()
+    assert len(s) == 25 and s[0] == 1.25 and s[-1] == 0.05
+    assert all(abs((a - b) - 0.05) < 1e-9 for a, b in zip(s, s[1:]))
+    assert set(bench.TABLE1) <= set(s)
+    for nproc, (cx, cy) in bench.CELL_SPLITS.items():
+        assert cx * cy == nproc and cx <= cy

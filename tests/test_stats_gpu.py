@@ -67,3 +67,33 @@ def test_cooling_protocol_bit_exact(precision):
     with pytest.raises(sco.ScoError) as e:
         g.set_temperature(0.0)
     assert e.value.status == sco.SCO_EINVAL
+
+
+def test_batched_cooling_matches_single_lattices():
+    # three replicas of the paper's model cooled on different schedules, n_sw = 5, temperature
+    # changes at multiples of n_sw: each replica equals a single lattice cooled the same way,
+    # and replica 0 the oracle
+    n_sw = 5
+    ps = [sco.make_params(L, T=1.25, J=1.0, D=0.1, seed=10 + L, n_sw=n_sw,
+                          precision=sco.FP32_GUARDED) for L in (24, 40, 17)]
+    sched = [(1.25, 0.8, 0.45), (1.0, 0.5, 0.05), (0.9, 0.9, 0.3)]
+    b = sco.Batch(ps)
+    lats = [sco.Lattice(p) for p in ps]
+    o = O.Chain(O.make_params(24, T=1.25, J=1.0, D=0.1, seed=34, n_sw=n_sw))
+    for k in range(3):
+        for r in range(3):
+            b.set_temperature(r, sched[r][k])
+            lats[r].set_temperature(sched[r][k])
+        o.set_temperature(sched[0][k])
+        b.run(2 * n_sw)
+        for lat in lats:
+            lat.sweep(2 * n_sw)
+        o.sweep(2 * n_sw)
+        for r in range(3):
+            assert np.array_equal(b.spins(r), lats[r].spins()), (k, r)
+            assert np.array_equal(b.accepts(r), lats[r].accepts()), (k, r)
+        assert np.array_equal(b.spins(0), o.spins()), k
+    b.run(2)
+    with pytest.raises(sco.ScoError) as e:
+        b.set_temperature(0, 0.5)  # step 32 is not a switch step
+    assert e.value.status == sco.SCO_ESTATE
