@@ -317,6 +317,8 @@ def run_ours(args, rank, world, local):
         t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
         out["e2e"] = dict(value=N * K * world / t_e2e, unit=UNIT, h2d_bytes_per_step=3 * N * 8,
                           d2h_bytes_per_step=3 * N * 8, steps=K)
+    if rank == 0:
+        out["graph_stats"] = graph_stats_report(lat)
     lat.close()
     del lat
     if not args.no_fp32:
@@ -350,6 +352,22 @@ def _timed_steps(lat, K, dev, stream):
         e1.record(stream)
     torch.cuda.synchronize(dev)
     return e0.elapsed_time(e1)
+
+
+def graph_stats_report(lat, n_rbins=32):
+    """Diagnostics of the lattice's current graph: P_survive per distance shell (Fig. 5), P_IPC
+    and the mean colour-count imbalance Delta R (Eq. (9)) of the Fig. 6 processor counts."""
+    out = {"p_ipc": {}, "delta_r_mean": {}, "delta_r_max": {}}
+    for nproc, (cx, cy) in CELL_SPLITS.items():
+        if cx > lat.params.Lx or cy > lat.params.Ly:
+            continue
+        st = lat.graph_stats(cx, cy, n_rbins)
+        out["p_ipc"][str(nproc)] = st["p_ipc"]
+        out["delta_r_mean"][str(nproc)] = st["delta_r_mean"]
+        out["delta_r_max"][str(nproc)] = st["delta_r_max"]
+    out["p_survive_r1_to_r%d" % n_rbins] = [float(x) for x in st["p_survive"]]
+    out["cell_splits"] = {str(k): v for k, v in CELL_SPLITS.items()}
+    return out
 
 
 def run_long(args, rank, world, dev, stream):
@@ -738,7 +756,7 @@ def main():
     line["fp64_peak"] = {"gflops": fpk["gflops"], "dfma_per_s": fpk["dfma_per_s"],
                          "expm1_per_s": fpk["expm1_per_s"], "log_per_s": fpk["log_per_s"],
                          "clocks": fpk["clocks"], "nominal_gflops": FP64_NOMINAL_GFLOPS}
-    for key in ("long", "precision", "kw_bound"):
+    for key in ("long", "precision", "kw_bound", "graph_stats"):
         if key in res:
             line[key] = res[key]
     if "batch" in res:
