@@ -357,7 +357,7 @@ def _timed_steps(lat, K, dev, stream):
 def graph_stats_report(lat, n_rbins=32):
     """Diagnostics of the lattice's current graph: P_survive per distance shell (Fig. 5), P_IPC
     and the mean colour-count imbalance Delta R (Eq. (9)) of the Fig. 6 processor counts."""
-    out = {"p_ipc": {}, "delta_r_mean": {}, "delta_r_max": {}}
+    out = {"p_ipc": {}, "delta_r_mean": {}, "delta_r_max": {}, "delta_r_weighted": {}}
     for nproc, (cx, cy) in CELL_SPLITS.items():
         if cx > lat.params.Lx or cy > lat.params.Ly:
             continue
@@ -365,6 +365,7 @@ def graph_stats_report(lat, n_rbins=32):
         out["p_ipc"][str(nproc)] = st["p_ipc"]
         out["delta_r_mean"][str(nproc)] = st["delta_r_mean"]
         out["delta_r_max"][str(nproc)] = st["delta_r_max"]
+        out["delta_r_weighted"][str(nproc)] = st["delta_r_weighted"]
     out["p_survive_r1_to_r%d" % n_rbins] = [float(x) for x in st["p_survive"]]
     out["cell_splits"] = {str(k): v for k, v in CELL_SPLITS.items()}
     return out
@@ -583,7 +584,7 @@ def run_protocol(args, local):
         key = min(TABLE1, key=lambda a: abs(a - T))
         if abs(key - T) > 1e-9:
             continue
-        ks, ds, dr, pipc, ps = [], [], [], {n: [] for n in CELL_SPLITS}, []
+        ks, ds, dr, drw, pipc, ps = [], [], [], [], {n: [] for n in CELL_SPLITS}, []
         for _ in range(args.proto_graphs):
             lat.sweep(n_sw)  # the epoch's graph is switched at its first step
             o = lat.observables()
@@ -594,6 +595,7 @@ def run_protocol(args, local):
                 pipc[nproc].append(st["p_ipc"])
                 if nproc == 288:
                     dr.append(st["delta_r_mean"])
+                    drw.append(st["delta_r_weighted"])
                     ps.append(st["p_survive"])
         o = lat.observables()
         k_m, k_s = _mean_sem(ks)
@@ -605,7 +607,8 @@ def run_protocol(args, local):
                      "e_switched_per_spin": o["e_switched"] / N,
                      "p_survive_r1_to_r16": [float(x) for x in pmean[:16]],
                      "p_ipc": {str(n): _mean_sem(v)[0] for n, v in pipc.items()},
-                     "delta_r_mean_288_cells": _mean_sem(dr)[0]})
+                     "delta_r_mean_288_cells": _mean_sem(dr)[0],
+                     "delta_r_weighted_288_cells": _mean_sem(drw)[0]})
     lat.close()
     t1 = time.perf_counter()
     # (2) M_phi(T): independent runs (seeds 0..R-1) as one batch

@@ -161,6 +161,8 @@ typedef struct {
   double p_ipc;        /* n_cross / n_pairs (0 without pairs) */
   double delta_r_mean; /* mean of Eq. (9) over the non-empty colours */
   double delta_r_max;  /* its maximum */
+  double delta_r_weighted; /* Eq. (9) weighted by class size: cells * sum_c K_max,c / N - 1
+                              (the sweep's time over cells against a balanced split, minus 1) */
   int32_t n_cells;     /* cells_x * cells_y */
   int32_t palette;     /* Delta + 1 */
 } sco_graph_stats;

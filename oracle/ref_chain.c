@@ -953,6 +953,7 @@ int sco_ref_graph_stats(const sco_ref_ctx* c, int32_t cells_x, int32_t cells_y, 
     ++K[(int64_t)c->colour[i] * ncell + cell_of(&c->p, i, cells_x, cells_y)];
   double sum = 0.0, dmax = 0.0;
   int32_t nonempty = 0;
+  int64_t kmax_sum = 0;
   for (int32_t col = 0; col < c->g; ++col) {
     int64_t tot = 0, kmax = 0;
     for (int64_t q = 0; q < ncell; ++q) {
@@ -960,6 +961,7 @@ int sco_ref_graph_stats(const sco_ref_ctx* c, int32_t cells_x, int32_t cells_y, 
       tot += k;
       if (k > kmax) kmax = k;
     }
+    kmax_sum += kmax;
     double dr = NAN;
     if (tot > 0) {
       const double kave = (double)tot / (double)ncell;
@@ -980,6 +982,8 @@ int sco_ref_graph_stats(const sco_ref_ctx* c, int32_t cells_x, int32_t cells_y, 
   out->p_ipc = ndip > 0 ? (double)ncross / (double)ndip : 0.0;
   out->delta_r_mean = nonempty > 0 ? sum / nonempty : 0.0;
   out->delta_r_max = dmax;
+  /* each class weighted by its size: the sweep of a colour lasts as long as its fullest cell */
+  out->delta_r_weighted = (double)(kmax_sum * ncell) / (double)c->N - 1.0;
   out->n_cells = (int32_t)ncell;
   out->palette = c->g;
   free(surv);

@@ -146,6 +146,7 @@ typedef struct {
   double p_ipc;        /* n_cross / n_pairs (0 without pairs) */
   double delta_r_mean; /* mean of Eq. (9) over the non-empty colours */
   double delta_r_max;
+  double delta_r_weighted; /* class-size-weighted mean: cells * sum_c K_max,c / N - 1 */
   int32_t n_cells;
   int32_t palette;
 } sco_ref_gstats;

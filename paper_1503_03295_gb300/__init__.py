@@ -58,7 +58,7 @@ class Obs(C.Structure):
 class GraphStats(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_cross", C.c_int64), ("p_ipc", C.c_double),
                 ("delta_r_mean", C.c_double), ("delta_r_max", C.c_double),
-                ("n_cells", C.c_int32), ("palette", C.c_int32)]
+                ("delta_r_weighted", C.c_double), ("n_cells", C.c_int32), ("palette", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -116,6 +116,12 @@ struct sco_ctx {
   bool colour_valid = false;
   uint32_t g = 1;
   uint64_t nnz = 0;
+  // FP64 form: the pair cache (hid parallel to col, keep arrays in SwitchBufs, upd per site);
+  // cache_state 0: keep holds the terms at the current spins; 1: carry from the last step's
+  // decisions first; 2: rebuild from the spins first
+  uint32_t* hid = nullptr;
+  uint8_t* upd = nullptr;
+  int cache_state = 0;
   int sticky = 0;
   unsigned long long ns_limit = 2000000000ull;  // bound of every device-side wait (2 s)
   // phase timing
@@ -193,6 +199,26 @@ cudaError_t grow(T*& ptr, uint64_t& cap, uint64_t need) {
   return e;
 }
 
+bool cache_on(const sco_ctx* c) { return c->sw.keep != nullptr; }
+
+// The three per-half-edge arrays of the pair cache for the current overflow capacity.
+cudaError_t alloc_keep(sco_ctx* c) {
+  cudaFree(c->sw.keep);
+  cudaFree(c->sw.keep_e);
+  cudaFree(c->sw.keep_l);
+  c->sw.keep = c->sw.keep_e = c->sw.keep_l = nullptr;
+  const size_t n = (size_t)c->P.N * kSlotCap + c->sw.ovf_cap;
+  cudaError_t e = cudaMalloc(&c->sw.keep, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->sw.keep_e, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->sw.keep_l, n * sizeof(double));
+  return e;
+}
+
+PairCache pair_cache(sco_ctx* c) {
+  if (!cache_on(c)) return PairCache{};
+  return PairCache{c->hid, c->sw.keep, c->sw.keep_e, c->sw.keep_l, c->upd};
+}
+
 sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4* src32) {
   PhaseTimer tm(c, kPhSwitch);
   // per-switch counters: n_half, n_dip, ovf_n, nnz and max_degree, max_degree_dip
@@ -215,6 +241,17 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4
     c->sw.ovf = nullptr;
     SCO_TRY(cudaMalloc(&c->sw.ovf, 2 * need * sizeof(uint32_t)));
     c->sw.ovf_cap = (uint32_t)need;
+    if (cache_on(c)) {
+      // half-edge ids must stay below 2^32 for the cache: else run without it
+      if ((uint64_t)c->P.N * kSlotCap + need >= (1ull << 32)) {
+        cudaFree(c->sw.keep);
+        cudaFree(c->sw.keep_e);
+        cudaFree(c->sw.keep_l);
+        c->sw.keep = c->sw.keep_e = c->sw.keep_l = nullptr;
+      } else {
+        SCO_TRY(alloc_keep(c));
+      }
+    }
     SCO_TRY(cudaMemsetAsync(c->cnt, 0, 4 * sizeof(unsigned long long), c->st));
     SCO_TRY(cudaMemsetAsync(&c->cnt->max_degree, 0, 2 * sizeof(unsigned), c->st));
     SCO_TRY(cudaMemsetAsync(&c->cnt->ovf_full, 0, sizeof(int), c->st));
@@ -226,9 +263,17 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4
     if (c->hcnt->ovf_n > c->sw.ovf_cap) return SCO_ECAPACITY;
   }
   c->nnz = c->hcnt->nnz;
+  if (cache_on(c) && c->hid && c->col_cap < c->nnz) {
+    cudaFree(c->hid);
+    c->hid = nullptr;
+  }
   SCO_TRY(grow(c->col, c->col_cap, c->nnz > 0 ? c->nnz : 1));
-  SCO_TRY(csr_fill(c->P, c->sw, c->row_ptr, c->col, c->hcnt->ovf_n > 0, c->cnt, c->st,
-                   &c->launches));
+  if (cache_on(c) && !c->hid) SCO_TRY(cudaMalloc(&c->hid, c->col_cap * sizeof(uint32_t)));
+  SCO_TRY(csr_fill(c->P, c->sw, c->row_ptr, c->col, cache_on(c) ? c->hid : nullptr,
+                   c->hcnt->ovf_n > 0, c->cnt, c->st, &c->launches));
+  // the switch left the FP64 terms of the switching spins in the cache: valid now unless the
+  // graph was switched from other spins (the epoch start of a restored checkpoint)
+  c->cache_state = src == c->s ? 0 : 2;
   c->g = c->hcnt->max_degree + 1;
   c->graph_epoch = epoch;
   c->colour_valid = false;
@@ -291,6 +336,11 @@ void free_all(sco_ctx* c) {
   cudaFree(c->sw.ocur);
   cudaFree(c->sw.ovf);
   cudaFree(c->sw.scan_tmp);
+  cudaFree(c->sw.keep);
+  cudaFree(c->sw.keep_e);
+  cudaFree(c->sw.keep_l);
+  cudaFree(c->hid);
+  cudaFree(c->upd);
   cudaFree(c->row_ptr);
   cudaFree(c->col);
   cudaFree(c->cb.word);
@@ -388,6 +438,13 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, sizeof(DevCounters), c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, N, c->st);
   if (e != cudaSuccess) return fail(from_cuda(e));
+  // the FP64 form keeps the pair cache while half-edge ids fit 32 bits
+  if (p->precision == SCO_FP64 && (uint64_t)N * kSlotCap + c->sw.ovf_cap < (1ull << 32)) {
+    e = alloc_keep(c);
+    if (e == cudaSuccess) e = cudaMalloc(&c->upd, N);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->upd, 0, N, c->st);
+    if (e != cudaSuccess) return fail(from_cuda(e));
+  }
   const uint64_t guess = (uint64_t)N * 24 + 1024;
   e = grow(c->col, c->col_cap, guess);
   if (e == cudaSuccess) e = spins_init(P, c->s, c->s32, c->st, &c->launches);
@@ -431,9 +488,14 @@ sco_status sco_sweep(sco_ctx* c, int32_t n_mcs) {
     if (st != SCO_OK) return st;
     {
       PhaseTimer tm(c, kPhSweep);
+      if (cache_on(c) && c->cache_state == 1)
+        SCO_TRY(cache_carry_run(c->P, c->sw, c->cb.colour, c->upd, c->cnt, c->st, &c->launches));
+      else if (cache_on(c) && c->cache_state == 2)
+        SCO_TRY(cache_build_run(c->P, c->tab, c->s, c->sw, c->cnt, c->st, &c->launches));
       SCO_TRY(sweep_run(c->P, c->tab, c->s, c->s32, c->row_ptr, c->col, c->cb.perm, c->cb.off,
                         c->g, (uint64_t)c->t, c->p.precision, c->acc, c->defer, c->cb.dcnt,
-                        c->prop, c->cnt, c->st, &c->launches));
+                        c->prop, c->cnt, pair_cache(c), c->st, &c->launches));
+      c->cache_state = 1;
     }
     c->t++;
   }
@@ -485,6 +547,7 @@ sco_status sco_set_spins(sco_ctx* c, const double* xyz, int32_t on_device) {
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
   SCO_TRY(spins_to_f32(c->P.N, c->s, c->s32, c->st, &c->launches));
   SCO_TRY(cudaStreamSynchronize(c->st));
+  c->cache_state = 2;  // the graph stays; its cached pair terms belong to the old spins
   return SCO_OK;
 }
 
@@ -699,7 +762,7 @@ sco_status sco_get_graph_stats(sco_ctx* c, int32_t cells_x, int32_t cells_y, int
   if (c->graph_epoch < 0 || !c->colour_valid) return SCO_ESTATE;
   const size_t nb = (size_t)n_rbins;
   std::vector<unsigned long long> cnt(2 * nb + 1);
-  std::vector<double> fo(5 + (size_t)c->g + nb);
+  std::vector<double> fo(6 + (size_t)c->g + nb);
   SCO_TRY(graph_stats_run(c->P, c->tab.disp, c->row_ptr, c->col, c->cb.colour, c->g, cells_x,
                           cells_y, n_rbins, c->st, &c->launches, cnt.data(), fo.data()));
   out->n_pairs = (int64_t)fo[0];
@@ -707,15 +770,16 @@ sco_status sco_get_graph_stats(sco_ctx* c, int32_t cells_x, int32_t cells_y, int
   out->p_ipc = fo[2];
   out->delta_r_mean = fo[3];
   out->delta_r_max = fo[4];
+  out->delta_r_weighted = fo[5];
   out->n_cells = cells_x * cells_y;
   out->palette = (int32_t)c->g;
   for (size_t b = 0; b < nb; ++b) {
     if (survived) survived[b] = (int64_t)cnt[b];
     if (pairs) pairs[b] = (int64_t)cnt[nb + b];
-    if (p_survive) p_survive[b] = fo[5 + c->g + b];
+    if (p_survive) p_survive[b] = fo[6 + c->g + b];
   }
   if (delta_r)
-    for (uint32_t k = 0; k < c->g; ++k) delta_r[k] = fo[5 + k];
+    for (uint32_t k = 0; k < c->g; ++k) delta_r[k] = fo[6 + k];
   return read_counters(c);
 }
 

@@ -80,15 +80,24 @@ struct SwitchBufs {
   uint32_t* ovf;    // 2 * ovf_cap (i, j | flag)
   uint32_t ovf_cap;
   uint64_t* scan_tmp;
+  // FP64 form only (else null): the pair cache, one value per half-edge id h (slot i * kSlotCap
+  // + q of site i, then N * kSlotCap + overflow index): keep = 1 - P_ij at the current spins,
+  // keep_e / keep_l = the same after the move of the endpoint that is updated first / last in
+  // the MC step (written by that endpoint whatever its decision).  N * kSlotCap + ovf_cap each.
+  double* keep;
+  double* keep_e;
+  double* keep_l;
 };
 cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float4* s32,
                        int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,
                        cudaStream_t st, int64_t* launches);
 cudaError_t csr_scan(const DevParams& P, SwitchBufs& b, uint32_t* row_ptr, DevCounters* cnt,
                      cudaStream_t st, int64_t* launches);
+// hid (optional, parallel to col): the half-edge id of every CSR entry (both entries of a pair
+// carry the id of its half-edge), sorted with its row.
 cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* row_ptr,
-                     uint32_t* col, bool has_overflow, DevCounters* cnt, cudaStream_t st,
-                     int64_t* launches);
+                     uint32_t* col, uint32_t* hid, bool has_overflow, DevCounters* cnt,
+                     cudaStream_t st, int64_t* launches);
 
 // ---- colour.cu ----
 struct ColourBufs {
@@ -119,15 +128,32 @@ cudaError_t bucket_run(const DevParams& P, uint32_t g, const uint32_t* row_ptr, 
                        DevCounters* cnt, cudaStream_t st, int64_t* launches);
 
 // ---- sweep.cu ----
+// The FP64 form's pair cache (see sweep_dev.cuh); hid null: no cache.
+struct PairCache {
+  const uint32_t* hid;  // per CSR entry: half-edge id of its pair
+  double* keep;         // per half-edge: 1 - P_ij at the MC step's start spins
+  double* keep_e;       // ... after the move of the endpoint decided first in the step
+  double* keep_l;       // ... after the move of the endpoint decided last
+  uint8_t* upd;         // per site in this MC step: 0 not decided, 1 rejected, 2 accepted
+};
 cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,
                       const uint32_t* off, uint32_t g, uint64_t step, int precision,
                       uint8_t* acc, uint32_t* defer, uint32_t* dcnt, double4_32a* prop,
-                      DevCounters* cnt, cudaStream_t st, int64_t* launches);
+                      DevCounters* cnt, const PairCache& pc, cudaStream_t st,
+                      int64_t* launches);
+// Between two MC steps on the same graph: carry the pair cache to the current spins (from the
+// last step's decisions), or rebuild it from the spins (after they changed outside the sweep).
+cudaError_t cache_carry_run(const DevParams& P, const SwitchBufs& b, const uint32_t* colour,
+                            const uint8_t* upd, const DevCounters* cnt, cudaStream_t st,
+                            int64_t* launches);
+cudaError_t cache_build_run(const DevParams& P, const Table& t, const double* s,
+                            const SwitchBufs& b, const DevCounters* cnt, cudaStream_t st,
+                            int64_t* launches);
 
 // ---- stats.cu ----
 // Graph diagnostics (see sco_get_graph_stats); copies 2 nb + 1 counts (survived, pairs, cross)
-// to h_counts and 5 + g + nb doubles (summary, Delta R per colour, P_survive) to h_out, then
+// to h_counts and 6 + g + nb doubles (summary, Delta R per colour, P_survive) to h_out, then
 // synchronises.
 cudaError_t graph_stats_run(const DevParams& P, const uint32_t* disp, const uint32_t* row_ptr,
                             const uint32_t* col, const uint32_t* colour, uint32_t g, int cx,

@@ -106,9 +106,9 @@ __global__ void __launch_bounds__(256) k_stats_final(uint32_t g, int64_t ncell, 
                                                      double* __restrict__ p_survive,
                                                      double* __restrict__ summary) {
   __shared__ double s_sum[256], s_max[256];
-  __shared__ unsigned long long s_ne[256], s_np[256];
+  __shared__ unsigned long long s_ne[256], s_np[256], s_km[256], s_nt[256];
   double sum = 0.0, mx = 0.0;
-  unsigned long long ne = 0, np = 0;
+  unsigned long long ne = 0, np = 0, km = 0, nt = 0;
   for (uint32_t c = threadIdx.x; c < g; c += blockDim.x) {
     unsigned long long tot = 0, kmax = 0;
     for (int64_t q = 0; q < ncell; ++q) {
@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(256) k_stats_final(uint32_t g, int64_t ncell, 
       tot += k;
       kmax = k > kmax ? k : kmax;
     }
+    km += kmax;
+    nt += tot;
     double dr = __longlong_as_double(0x7FF8000000000000ll);  // NaN: empty colour
     if (tot > 0) {
       const double kave = (double)tot / (double)ncell;
@@ -135,21 +137,26 @@ __global__ void __launch_bounds__(256) k_stats_final(uint32_t g, int64_t ncell, 
   s_max[threadIdx.x] = mx;
   s_ne[threadIdx.x] = ne;
   s_np[threadIdx.x] = np;
+  s_km[threadIdx.x] = km;
+  s_nt[threadIdx.x] = nt;
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0, m = 0.0;
-    unsigned long long n = 0, p = 0;
+    unsigned long long n = 0, p = 0, kms = 0, nts = 0;
     for (int t = 0; t < (int)blockDim.x; ++t) {
       a += s_sum[t];
       m = fmax(m, s_max[t]);
       n += s_ne[t];
       p += s_np[t];
+      kms += s_km[t];
+      nts += s_nt[t];
     }
     summary[0] = (double)p;                                    // surviving dipolar pairs
     summary[1] = (double)*cross;                               // of which across cells
     summary[2] = p > 0 ? (double)*cross / (double)p : 0.0;     // P_IPC
     summary[3] = n > 0 ? a / (double)n : 0.0;                  // mean Delta R
     summary[4] = m;                                            // max Delta R
+    summary[5] = (double)(kms * (unsigned long long)ncell) / (double)nts - 1.0;  // weighted
   }
 }
 
@@ -161,7 +168,7 @@ cudaError_t graph_stats_run(const DevParams& P, const uint32_t* disp, const uint
                             unsigned long long* h_counts, double* h_out) {
   // device scratch: survived, pairs, cross (u64), summary, delta_r, p_survive (f64), counts
   const int64_t ncell = (int64_t)cx * cy;
-  const size_t n64 = 2 * (size_t)nb + 1, nf = 5 + (size_t)g + nb;
+  const size_t n64 = 2 * (size_t)nb + 1, nf = 6 + (size_t)g + nb;
   const size_t ncnt = (size_t)g * ncell;
   char* buf = nullptr;
   const size_t bytes = 8 * (n64 + nf) + 4 * ncnt;
@@ -178,8 +185,8 @@ cudaError_t graph_stats_run(const DevParams& P, const uint32_t* disp, const uint
     k_pair_shells<<<grid, 256, 0, st>>>(P, disp, nb, pairs);
     k_edge_stats<<<grid, 256, 0, st>>>(P, row_ptr, col, nb, cx, cy, surv, cross);
     k_colour_cells<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P, colour, g, cx, cy, counts);
-    k_stats_final<<<1, 256, 0, st>>>(g, ncell, nb, counts, surv, pairs, cross, fout + 5,
-                                     fout + 5 + g, fout);
+    k_stats_final<<<1, 256, 0, st>>>(g, ncell, nb, counts, surv, pairs, cross, fout + 6,
+                                     fout + 6 + g, fout);
     *launches += 4;
     e = cudaGetLastError();
   }

@@ -129,6 +129,108 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
   return 2;
 }
 
+// The pair cache of the FP64 form (single lattice).  For every surviving dipolar pair (half-edge
+// id h, carried by both CSR entries of the pair) keep[h] holds 1 - P = -expm1(x) of the pair at
+// the spins of the MC step's start (the switch leaves its FP64 value there), with the error of
+// any FP64 evaluation of that term (|x error| <= c0 + 2^-52 |x|, relative error of the
+// elementary function within kExpm1RelErr6).  While a site is decided it writes the term at its
+// proposed spin: into keep_e[h] when the other endpoint comes later in the step, into keep_l[h]
+// when it came earlier; upd[i] records that site i is done (1 rejected, 2 accepted).  So the
+// old-spin term of a pair is keep[h], or keep_e[h] when the earlier endpoint moved: one of the
+// two expm1 evaluations per pair is read instead of computed.  A written value <= 0 (the
+// proposed x not strictly negative in FP64) makes every reader leave its decision to the
+// double-double path, which does not use the cache.
+// accept_fp64 with the old-spin terms from the pair cache; writes the proposed-spin term of
+// every pair (the loop visits every pair, also when the decision is already undecided).
+__device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const SiteCtx& c,
+                                                  const Sw64* __restrict__ sw,
+                                                  const double* __restrict__ s,
+                                                  const uint32_t* __restrict__ row_ptr,
+                                                  const uint32_t* __restrict__ col,
+                                                  const PairCache& pc) {
+  const double S0 = c.S[0], S1 = c.S[1], S2 = c.S[2];
+  const double N0 = c.Sn[0], N1 = c.Sn[1], N2 = c.Sn[2];
+  double bdv = 0.0, pz_o = 1.0, pz_n = 1.0;
+  unsigned long long c0m = 0;
+  int dmax = -2046;
+  const unsigned long long small_b = pos_bits(0x1p-600);
+  int sc_o = 0, sc_n = 0, n = 0;
+  bool bad = false;
+  const uint32_t e1 = row_ptr[c.i + 1];
+  for (uint32_t e = row_ptr[c.i]; e < e1; ++e) {
+    const uint32_t cj = col[e];
+    if (cj & kExchOnly) continue;
+    const int64_t j = cj;
+    const uint32_t h = pc.hid[e];
+    const uint32_t uj = pc.upd[j];
+    const uint32_t yj = site_row((uint32_t)j, P);
+    const int32_t dx = (int32_t)((uint32_t)j - yj * (uint32_t)P.Lx) - c.xi;
+    const int32_t dy = (int32_t)yj - c.yi;
+    const Sw64& t = sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
+    const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
+    const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
+    const double a1 = t.a1, bvm = t.bvm;
+    const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
+    const double zo = uj == 2u ? pc.keep_e[h] : pc.keep[h];
+    const double tp = bx * ax3 + by * ay3;
+    const double gx = a1 * bx - tp * fx;
+    const double gy = a1 * by - tp * fy;
+    const double gz = a1 * bz;
+    const double xn = fma(N0, gx, fma(N1, gy, fma(N2, gz, -bvm)));
+    const double xo = fma(S0, gx, fma(S1, gy, fma(S2, gz, -bvm)));
+    const bool okn = neg_strict(xn);
+    const double zn = okn ? -expm1_np6(xn) : -1.0;
+    if (uj == 0u) pc.keep_e[h] = zn;
+    else pc.keep_l[h] = zn;
+    // the cached term must be a positive number (a non-positive one marks an FP64 evaluation
+    // that could not be trusted)
+    if (!okn || !neg_strict(xo) || !(pos_bits(zo) - 1ull < 0x7FEFFFFFFFFFFFFFull)) {
+      bad = true;
+      continue;
+    }
+    pz_n *= zn;
+    pz_o *= zo;
+    if (pos_bits(pz_n) < small_b) { pz_n *= 0x1p600; ++sc_n; }
+    if (pos_bits(pz_o) < small_b) { pz_o *= 0x1p600; ++sc_o; }
+    bdv += xn - xo;
+    dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
+    c0m = max(c0m, pos_bits(t.c0));
+    ++n;
+  }
+  if (bad) return 2;
+  if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;  // n <= 2^(32 - clz n)
+  const double lin = n > 0 && dmax + 2 >= -1022
+                         ? (double)n * __longlong_as_double((long long)(dmax + 2 + 1023) << 52)
+                         : 0.0;
+  double tex = 0.0, bex = 0.0;
+  if (P.J != 0.0) {
+    double h0 = 0.0, h1 = 0.0, h2 = 0.0;
+    const int64_t nb[4] = {c.xi > 0 ? c.i - 1 : -1, c.xi + 1 < P.Lx ? c.i + 1 : -1,
+                           c.yi > 0 ? c.i - P.Lx : -1, c.yi + 1 < P.Ly ? c.i + P.Lx : -1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (nb[q] < 0) continue;
+      h0 += s[nb[q]];
+      h1 += s[P.N + nb[q]];
+      h2 += s[2 * P.N + nb[q]];
+    }
+    const double dot = (c.Sn[0] - c.S[0]) * h0 + (c.Sn[1] - c.S[1]) * h1 + (c.Sn[2] - c.S[2]) * h2;
+    tex = -(P.beta * P.J) * dot;
+    bex = 0x1p-44 * fabs(P.beta * P.J);
+  }
+  const double lo = log_np(pz_o), ln = log_np(pz_n);
+  const double scale = (double)((sc_n - sc_o) * kScale64) * P.ln2_hi;
+  const double lu = log_np(c.u);
+  const double mu = lu + ((bdv + tex) + ((lo - ln) + scale));
+  const double c0s = (double)n * __longlong_as_double((long long)c0m);
+  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
+                          kLogRelErr * (fabs(lo) + fabs(ln) + fabs(lu)) + bex +
+                          0x1p-51 * (fabs(scale) + fabs(tex) + fabs(bdv) + fabs(mu)));
+  if (mu < -B) return 1;
+  if (mu > B) return 0;
+  return 2;
+}
+
 // FP32 screen of the same decision: shadow spins (|dS| <= 2^-24 per component), FP32 table
 // constants, CUDA's single-precision expm1f / logf (<= 1 ulp; 4x margin: eps_f = 2^-21),
 // eps_r = 2^-23, and a compensated (Neumaier) sum of the V' - V terms.
@@ -346,6 +448,94 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
   if (bad) return 2;
   if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;
   // n 2^(dmax + 2), the power of two from its bits (dmax + 2 <= -10 here; below -1022: 0)
+  const double lin = n > 0 && dmax + 2 >= -1022
+                         ? (double)n * __longlong_as_double((long long)(dmax + 2 + 1023) << 52)
+                         : 0.0;
+  double tex = 0.0, bex = 0.0;
+  if (P.J != 0.0) {
+    double h0 = 0.0, h1 = 0.0, h2 = 0.0;
+    const int64_t nb[4] = {c.xi > 0 ? c.i - 1 : -1, c.xi + 1 < P.Lx ? c.i + 1 : -1,
+                           c.yi > 0 ? c.i - P.Lx : -1, c.yi + 1 < P.Ly ? c.i + P.Lx : -1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (nb[q] < 0) continue;
+      h0 += s[nb[q]];
+      h1 += s[P.N + nb[q]];
+      h2 += s[2 * P.N + nb[q]];
+    }
+    const double dot = (c.Sn[0] - c.S[0]) * h0 + (c.Sn[1] - c.S[1]) * h1 + (c.Sn[2] - c.S[2]) * h2;
+    tex = -(P.beta * P.J) * dot;
+    bex = 0x1p-44 * fabs(P.beta * P.J);
+  }
+  const double lu = log_np(c.u);
+  const double mu = lu + ((bdv + tex) + lsum);
+  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
+                          kLogRelErr * (labs + fabs(lu)) + 0x1p-49 * labs + bex +
+                          0x1p-51 * (fabs(tex) + fabs(bdv) + fabs(mu)));
+  if (mu < -B) return 1;
+  if (mu > B) return 0;
+  return 2;
+}
+
+// accept_fp64_warp with the pair cache (see accept_fp64_cached); every lane writes the
+// proposed-spin terms of its pairs.
+__device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
+                                       const Sw64* __restrict__ sw,
+                                       const double* __restrict__ s,
+                                       const uint32_t* __restrict__ row_ptr,
+                                       const uint32_t* __restrict__ col, const PairCache& pc,
+                                       int lane) {
+  double bdv = 0.0, pz_o = 1.0, pz_n = 1.0, c0s = 0.0;
+  int sc_o = 0, sc_n = 0, n = 0, bad = 0, dmax = -2046;
+  const uint32_t e1 = row_ptr[c.i + 1];
+  for (uint32_t e = row_ptr[c.i] + lane; e < e1; e += 32) {
+    const uint32_t cj = col[e];
+    if (cj & kExchOnly) continue;
+    const uint32_t j = cj;
+    const uint32_t h = pc.hid[e];
+    const uint32_t uj = pc.upd[j];
+    const uint32_t yj = site_row(j, P);
+    const int32_t dx = (int32_t)(j - yj * (uint32_t)P.Lx) - c.xi;
+    const int32_t dy = (int32_t)yj - c.yi;
+    const Sw64& t = sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)];
+    const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
+    const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
+    const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
+    const double zo = uj == 2u ? pc.keep_e[h] : pc.keep[h];
+    const double tp = bx * ax3 + by * ay3;
+    const double gx = t.a1 * bx - tp * fx;
+    const double gy = t.a1 * by - tp * fy;
+    const double gz = t.a1 * bz;
+    const double xn = fma(c.Sn[0], gx, fma(c.Sn[1], gy, fma(c.Sn[2], gz, -t.bvm)));
+    const double xo = fma(c.S[0], gx, fma(c.S[1], gy, fma(c.S[2], gz, -t.bvm)));
+    const bool okn = neg_strict(xn);
+    const double zn = okn ? -expm1_np6(xn) : -1.0;
+    if (uj == 0u) pc.keep_e[h] = zn;
+    else pc.keep_l[h] = zn;
+    if (!okn || !neg_strict(xo) || !(pos_bits(zo) - 1ull < 0x7FEFFFFFFFFFFFFFull)) {
+      bad = 1;
+      continue;
+    }
+    pz_n *= zn;
+    pz_o *= zo;
+    if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
+    if (pz_o < 0x1p-600) { pz_o *= 0x1p600; ++sc_o; }
+    bdv += xn - xo;
+    dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
+    c0s += t.c0;
+    ++n;
+  }
+  const double lo = log_np(pz_o) - (double)(sc_o * kScale64) * P.ln2_hi;
+  const double ln = log_np(pz_n) - (double)(sc_n * kScale64) * P.ln2_hi;
+  const double lsum = warp_sum_d(lo - ln);
+  const double labs = warp_sum_d(fabs(lo) + fabs(ln));
+  bdv = warp_sum_d(bdv);
+  c0s = warp_sum_d(c0s);
+  dmax = __reduce_max_sync(0xffffffffu, dmax);
+  n = __reduce_add_sync(0xffffffffu, n);
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (bad) return 2;
+  if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;
   const double lin = n > 0 && dmax + 2 >= -1022
                          ? (double)n * __longlong_as_double((long long)(dmax + 2 + 1023) << 52)
                          : 0.0;

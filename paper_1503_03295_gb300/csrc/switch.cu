@@ -34,7 +34,11 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 5 : 4) k_switch(const DevPara
   __syncthreads();
   const NearTable T{sW, sD, W, disp, nnear, P.K};
   const uint64_t Wtot = P.K > 0 ? __ldg(&W[P.K - 1]) : 0;
-  const SwitchOut o{b.hslot, b.indeg, b.ovf, b.ovf_cap, &cnt->ovf_n, &cnt->ovf_full};
+  SwitchOut o{b.hslot, b.indeg, b.ovf, b.ovf_cap, &cnt->ovf_n, &cnt->ovf_full};
+  if (PREC == 0 && b.keep) {
+    o.keep = b.keep;
+    o.keep_ovf = b.keep + (size_t)P.N * kSlotCap;
+  }
   const uint32_t N = (uint32_t)P.N;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned below = (1u << lane) - 1u;
@@ -105,10 +109,11 @@ __global__ void k_degree(int64_t N, const uint32_t* __restrict__ hcnt,
 
 // Row i holds its lower neighbours (j < i, scattered here by the sites j) followed by its
 // upper neighbours (written by site i from its slots).  Rows are sorted afterwards.
+// hid (optional): both entries of a pair get the half-edge id i * kSlotCap + q.
 __global__ void k_fill(int64_t N, const uint32_t* __restrict__ hslot,
                        const uint32_t* __restrict__ hcnt, const uint32_t* __restrict__ indeg,
                        const uint32_t* __restrict__ row_ptr, uint32_t* __restrict__ lcur,
-                       uint32_t* __restrict__ col) {
+                       uint32_t* __restrict__ col, uint32_t* __restrict__ hid) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint32_t n = min(hcnt[i], (uint32_t)kSlotCap);
@@ -116,21 +121,36 @@ __global__ void k_fill(int64_t N, const uint32_t* __restrict__ hslot,
   for (uint32_t q = 0; q < n; ++q) {
     const uint32_t jv = hslot[i * (int64_t)kSlotCap + q];
     const uint32_t j = jv & kIndexMask;
+    const uint32_t lo = row_ptr[j] + atomicAdd(&lcur[j], 1u);
     col[up + q] = jv;
-    col[row_ptr[j] + atomicAdd(&lcur[j], 1u)] = (uint32_t)i | (jv & kExchOnly);
+    col[lo] = (uint32_t)i | (jv & kExchOnly);
+    if (hid) {
+      const uint32_t h = (uint32_t)i * (uint32_t)kSlotCap + q;
+      hid[up + q] = h;
+      hid[lo] = h;
+    }
   }
 }
 
-__global__ void k_fill_ovf(unsigned long long n, const uint32_t* __restrict__ ovf,
+// Overflow half-edge q: id N * kSlotCap + q.
+__global__ void k_fill_ovf(unsigned long long n, uint32_t N, const uint32_t* __restrict__ ovf,
                            const uint32_t* __restrict__ indeg,
                            const uint32_t* __restrict__ row_ptr, uint32_t* __restrict__ lcur,
-                           uint32_t* __restrict__ ocur, uint32_t* __restrict__ col) {
+                           uint32_t* __restrict__ ocur, uint32_t* __restrict__ col,
+                           uint32_t* __restrict__ hid) {
   const unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
   if (q >= n) return;
   const uint32_t i = ovf[2 * q], jv = ovf[2 * q + 1];
   const uint32_t j = jv & kIndexMask;
-  col[row_ptr[i] + indeg[i] + kSlotCap + atomicAdd(&ocur[i], 1u)] = jv;
-  col[row_ptr[j] + atomicAdd(&lcur[j], 1u)] = i | (jv & kExchOnly);
+  const uint32_t up = row_ptr[i] + indeg[i] + kSlotCap + atomicAdd(&ocur[i], 1u);
+  const uint32_t lo = row_ptr[j] + atomicAdd(&lcur[j], 1u);
+  col[up] = jv;
+  col[lo] = i | (jv & kExchOnly);
+  if (hid) {
+    const uint32_t h = N * (uint32_t)kSlotCap + (uint32_t)q;
+    hid[up] = h;
+    hid[lo] = h;
+  }
 }
 
 __global__ void k_rowsort(int64_t N, const uint32_t* __restrict__ row_ptr,
@@ -138,6 +158,19 @@ __global__ void k_rowsort(int64_t N, const uint32_t* __restrict__ row_ptr,
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned nd = 0;
   if (i < N) nd = sort_row(col + row_ptr[i], row_ptr[i + 1] - row_ptr[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nd = max(nd, __shfl_down_sync(0xffffffffu, nd, o));
+  if ((threadIdx.x & 31) == 0 && nd) atomicMax(&cnt->max_degree_dip, nd);
+}
+
+// The same with the half-edge ids moved along with their entries.
+__global__ void k_rowsort_pay(int64_t N, const uint32_t* __restrict__ row_ptr,
+                              uint32_t* __restrict__ col, uint32_t* __restrict__ hid,
+                              DevCounters* __restrict__ cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned nd = 0;
+  if (i < N)
+    nd = sort_row_pay(col + row_ptr[i], hid + row_ptr[i], row_ptr[i + 1] - row_ptr[i]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nd = max(nd, __shfl_down_sync(0xffffffffu, nd, o));
   if ((threadIdx.x & 31) == 0 && nd) atomicMax(&cnt->max_degree_dip, nd);
@@ -183,12 +216,12 @@ cudaError_t csr_scan(const DevParams& P, SwitchBufs& b, uint32_t* row_ptr, DevCo
 }
 
 cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* row_ptr,
-                     uint32_t* col, bool has_overflow, DevCounters* cnt, cudaStream_t st,
-                     int64_t* launches) {
+                     uint32_t* col, uint32_t* hid, bool has_overflow, DevCounters* cnt,
+                     cudaStream_t st, int64_t* launches) {
   cudaError_t e = cudaMemsetAsync(b.lcur, 0, P.N * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((P.N + 255) / 256);
-  k_fill<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, b.indeg, row_ptr, b.lcur, col);
+  k_fill<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, b.indeg, row_ptr, b.lcur, col, hid);
   ++*launches;
   if (has_overflow) {
     unsigned long long n = 0;
@@ -199,12 +232,13 @@ cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* ro
     e = cudaMemsetAsync(b.ocur, 0, P.N * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-      k_fill_ovf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, b.ovf, b.indeg, row_ptr, b.lcur,
-                                                              b.ocur, col);
+      k_fill_ovf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, (uint32_t)P.N, b.ovf, b.indeg,
+                                                              row_ptr, b.lcur, b.ocur, col, hid);
       ++*launches;
     }
   }
-  k_rowsort<<<nb, 256, 0, st>>>(P.N, row_ptr, col, cnt);
+  if (hid) k_rowsort_pay<<<nb, 256, 0, st>>>(P.N, row_ptr, col, hid, cnt);
+  else k_rowsort<<<nb, 256, 0, st>>>(P.N, row_ptr, col, cnt);
   ++*launches;
   return cudaGetLastError();
 }

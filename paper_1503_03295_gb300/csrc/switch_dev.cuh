@@ -183,20 +183,30 @@ __device__ __noinline__ bool survives_dd(const DevParams& P, const double* Si, c
   return dd_lt(dd_mul_d(q, u1), pr);
 }
 
-// FP64 survival test u q < 1 - P_ij: x = beta (V - Vmax) from the beta-scaled pair table
-// (t, the sweep's Sw64 entry), 1 - P = -expm1_np(x), margin bound t.bsw (precomputed: |dx| <=
-// c0, expm1_np within kExpm1RelErr, q within 2^-50, two roundings; doubled).  u is exact.
-__device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t, double q,
-                                              const double* Si, const double* Sj, int32_t dx,
-                                              int32_t dy, uint64_t A, double u1,
-                                              unsigned& ghits) {
+// 1 - P_ij = -expm1(beta (V - Vmax)) of the pair (S_i at i, S_j at i + (dx, dy)) in FP64 from the
+// beta-scaled pair table t: x = a1 (S_i.S_j) - (S_i.a3 d)(S_j.d) - bvm, |x error| <= c0 +
+// 2^-52 |x| (c0 covers the roundings), then expm1_np (relative error kExpm1RelErr).
+__device__ __forceinline__ double pair_keep64(const Sw64& t, const double* Si, const double* Sj,
+                                              int32_t dx, int32_t dy) {
   const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
   const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
   const double ss = Si[0] * Sj[0] + Si[1] * Sj[1] + Si[2] * Sj[2];
   const double pa = Si[0] * ax3 + Si[1] * ay3;
   const double pb = Sj[0] * fx + Sj[1] * fy;
   const double b = fma(t.a1, ss, fma(-pa, pb, -t.bvm));  // c0 covers these two roundings
-  const double pr = -expm1_np(b);
+  return -expm1_np(b);
+}
+
+// FP64 survival test u q < 1 - P_ij: x = beta (V - Vmax) from the beta-scaled pair table
+// (t, the sweep's Sw64 entry), 1 - P = -expm1_np(x), margin bound t.bsw (precomputed: |dx| <=
+// c0, expm1_np within kExpm1RelErr, q within 2^-50, two roundings; doubled).  u is exact.
+// `keep` receives the FP64 value of 1 - P (within its error bound whatever the decision).
+__device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t, double q,
+                                              const double* Si, const double* Sj, int32_t dx,
+                                              int32_t dy, uint64_t A, double u1,
+                                              unsigned& ghits, double& keep) {
+  const double pr = pair_keep64(t, Si, Sj, dx, dy);
+  keep = pr;
   const double mu = pr - u1 * q;
   // mu > bsw, mu < -bsw on ordered bit images (bsw > 0: ord(-bsw) = -ord(bsw) - 1)
   const long long om = ord_bits(mu), ob = ord_bits(t.bsw);
@@ -239,12 +249,15 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
   const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy);
   const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
   const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-  return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, A, u53(wU), ghits);
+  double keep;
+  return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, A, u53(wU), ghits, keep);
 }
 
 // Where a site writes its upper neighbours: kSlotCap slots of its own (row `id` of hslot), then
 // an overflow list shared by all sites (entry: site id, j | flag).  indeg counts lower
-// neighbours per (local) site.
+// neighbours per (local) site.  keep / keep_ovf (optional, FP64 form): the FP64 value of
+// 1 - P_ij of each surviving dipolar pair, at the same slot or overflow index (the pair cache
+// that the FP64 sweep starts from).
 struct SwitchOut {
   uint32_t* hslot;
   uint32_t* indeg;
@@ -252,6 +265,8 @@ struct SwitchOut {
   uint32_t ovf_cap;
   unsigned long long* ovf_n;
   int* status;
+  double* keep = nullptr;
+  double* keep_ovf = nullptr;
 };
 
 // One site's walk along its half-plane list: the candidate search of Sec. 2.1 with the state it
@@ -273,14 +288,16 @@ struct SiteWalk {
 };
 
 __device__ __forceinline__ void switch_emit(const SwitchOut& o, uint32_t id, uint32_t& n_out,
-                                            uint32_t jv) {
+                                            uint32_t jv, double keep = 0.0) {
   if (n_out < (uint32_t)kSlotCap) {
     o.hslot[(size_t)id * kSlotCap + n_out] = jv;
+    if (o.keep) o.keep[(size_t)id * kSlotCap + n_out] = keep;
   } else {
     const unsigned long long idx = atomicAdd(o.ovf_n, 1ull);
     if (idx < o.ovf_cap) {
       o.ovf[2 * idx] = id;
       o.ovf[2 * idx + 1] = jv;
+      if (o.keep) o.keep_ovf[idx] = keep;
     } else {
       set_status(o.status, kStatusCapacity);
     }
@@ -344,6 +361,7 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
     const uint64_t A = Wk - (k > 0 ? T.w(k - 1) : 0ull);
     const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
     bool surv;
+    double keep = 0.0;
     if (PREC == 1) {
       const float4 sj = s32[j];
       const float Sj32[3] = {sj.x, sj.y, sj.z};
@@ -351,10 +369,11 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
                            (int64_t)a.i, j, dx, dy, A, wU, g32, ghits);
     } else {
       const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-      surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), a.Si, Sj, dx, dy, A, u53(wU), ghits);
+      surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), a.Si, Sj, dx, dy, A, u53(wU), ghits,
+                           keep);
     }
     if (surv) {
-      switch_emit(o, a.id, a.n_out, (uint32_t)j);
+      switch_emit(o, a.id, a.n_out, (uint32_t)j, keep);
       ++n_dip;
       if (k == mnn0) a.nn0 = true;
       if (k == mnn1) a.nn1 = true;
@@ -447,6 +466,67 @@ __device__ __forceinline__ unsigned sort_row(uint32_t* __restrict__ r, uint32_t 
         --c;
       }
       r[c] = x;
+    }
+    for (uint32_t a = 0; a < n; ++a) nd += (r[a] & kExchOnly) ? 0u : 1u;
+  }
+  return nd;
+}
+
+// Compare-exchange on the neighbour index, its payload (pair id) travelling with it.
+__device__ __forceinline__ void row_ce2(uint32_t& a, uint32_t& b, uint32_t& pa, uint32_t& pb) {
+  const bool sw = (a & kIndexMask) > (b & kIndexMask);
+  const uint32_t lo = sw ? b : a, hi = sw ? a : b;
+  const uint32_t plo = sw ? pb : pa, phi = sw ? pa : pb;
+  a = lo;
+  b = hi;
+  pa = plo;
+  pb = phi;
+}
+
+// sort_row with a payload per entry (pe, moved with its entry).
+__device__ __forceinline__ unsigned sort_row_pay(uint32_t* __restrict__ r, uint32_t* __restrict__ pe,
+                                                 uint32_t n) {
+  unsigned nd = 0;
+  if (n <= 32) {
+    uint32_t v[32], w[32];
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      v[a] = (uint32_t)a < n ? r[a] : 0xFFFFFFFFu;
+      w[a] = (uint32_t)a < n ? pe[a] : 0u;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 32; ++a) {
+          const int l = a ^ j;
+          if (l > a) {
+            if ((a & k) == 0) row_ce2(v[a], v[l], w[a], w[l]);
+            else row_ce2(v[l], v[a], w[l], w[a]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      if ((uint32_t)a < n) {
+        r[a] = v[a];
+        pe[a] = w[a];
+        nd += (v[a] & kExchOnly) ? 0u : 1u;
+      }
+    }
+  } else {
+    for (uint32_t a = 1; a < n; ++a) {
+      const uint32_t x = r[a], px = pe[a];
+      uint32_t c = a;
+      while (c > 0 && (r[c - 1] & kIndexMask) > (x & kIndexMask)) {
+        r[c] = r[c - 1];
+        pe[c] = pe[c - 1];
+        --c;
+      }
+      r[c] = x;
+      pe[c] = px;
     }
     for (uint32_t a = 0; a < n; ++a) nd += (r[a] & kExchOnly) ? 0u : 1u;
   }

@@ -108,6 +108,11 @@ def test_colour_imbalance_one_cell_and_recount():
             assert st["delta_r"][c] == pytest.approx(drs[-1], rel=1e-15)
         assert st["delta_r_mean"] == pytest.approx(np.mean(drs), rel=1e-14)
         assert st["delta_r_max"] == pytest.approx(np.max(drs), rel=1e-15)
+        # class-size weighted: sum_c |c| Delta R_c / N = cells sum_c K_max,c / N - 1
+        kmax = [np.bincount(cell[col == c], minlength=cx * cy).max() for c in range(st["palette"])]
+        assert st["delta_r_weighted"] == pytest.approx(cx * cy * sum(kmax) / (L * L) - 1,
+                                                       rel=1e-14, abs=1e-15)
+    assert ch.graph_stats(1, 1, 4)["delta_r_weighted"] == 0.0
 
 
 def test_set_temperature_rebuilds_the_graph_at_the_new_beta():

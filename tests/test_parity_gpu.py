@@ -257,3 +257,35 @@ def test_library_log_within_its_bound():
     err, diff = sco.selftest_log(1 << 24, seed=5)
     assert err < 2.0 ** -49
     assert diff < 2.0 ** -49
+
+
+def test_fp64_pair_cache_paths_bit_exact():
+    """The FP64 form carries the pair terms of one MC step to the next on the same graph
+    (n_sw > 1), rebuilds them after spins were set from outside, and starts from the switch's
+    values after every switch: with exchange bonds in the graph, every path keeps the accept bits
+    and spins equal to the oracle's."""
+    L = 40
+    p = dict(T=0.35, J=0.5, D=1.0, seed=13, n_sw=4)
+    g, o = _pair(L, **p)
+    rng = np.random.default_rng(3)
+    plan = [5, "same", 3, "new", 6, 4]
+    for step in plan:
+        if step == "same":  # set_spins with the current spins: cached terms rebuilt, same values
+            x = g.spins()
+            g.set_spins(x)
+            o.set_spins(x)
+            continue
+        if step == "new":  # fresh spins in the middle of an epoch: the graph stays
+            v = rng.normal(size=(L * L, 3))
+            v /= np.linalg.norm(v, axis=1, keepdims=True)
+            x = v.T.reshape(-1).copy()
+            g.set_spins(x)
+            o.set_spins(x)
+            continue
+        for _ in range(step):
+            g.sweep(1)
+            o.sweep(1)
+            assert np.array_equal(g.accepts(), o.accepts())
+        assert np.array_equal(g.spins(), o.spins())
+    og, oo = g.observables(), o.observables()
+    _same_energy(og["e_switched"], oo["e_switched"], g.N)

@@ -22,6 +22,7 @@ def _same_stats(a, b):
     assert np.array_equal(a["p_survive"], b["p_survive"], equal_nan=True)
     assert np.array_equal(a["delta_r"], b["delta_r"], equal_nan=True)
     assert a["delta_r_max"] == b["delta_r_max"]
+    assert a["delta_r_weighted"] == b["delta_r_weighted"]
     assert abs(a["delta_r_mean"] - b["delta_r_mean"]) <= 1e-14 * max(abs(b["delta_r_mean"]), 1.0)
 
 
