@@ -117,7 +117,9 @@ sco_status sco_set_spins(sco_ctx* c, const double* xyz, int32_t on_device);
 sco_status sco_get_sizes(sco_ctx* c, int64_t* n_sites, int64_t* n_entries, int32_t* max_degree,
                          int32_t* palette);
 
-/* Host copies of the graph: row_ptr (N + 1), col (n_entries), colour (N); NULL skips. */
+/* Host copies of the graph: row_ptr (N + 1), col (n_entries), colour (N); NULL skips.  col
+ * comes with every row sorted by neighbour index (the library keeps its own rows in an internal
+ * order, which changes no result; the copy is sorted on the device first). */
 sco_status sco_get_graph(sco_ctx* c, uint32_t* row_ptr, uint32_t* col, uint32_t* colour);
 
 /* Host copies of the colour classes: perm (N sites grouped by colour: off[c] .. off[c+1] - 1

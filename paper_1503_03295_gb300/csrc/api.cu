@@ -122,6 +122,7 @@ struct sco_ctx {
   uint32_t* hid = nullptr;
   uint8_t* upd = nullptr;
   int cache_state = 0;
+  bool dip_valid = false;  // cnt->max_degree_dip holds the dipolar Delta of the current graph
   int sticky = 0;
   unsigned long long ns_limit = 2000000000ull;  // bound of every device-side wait (2 s)
   // phase timing
@@ -269,8 +270,10 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4
   }
   SCO_TRY(grow(c->col, c->col_cap, c->nnz > 0 ? c->nnz : 1));
   if (cache_on(c) && !c->hid) SCO_TRY(cudaMalloc(&c->hid, c->col_cap * sizeof(uint32_t)));
+  // rows are left unsorted (their order changes no result); getters sort their copies
   SCO_TRY(csr_fill(c->P, c->sw, c->row_ptr, c->col, cache_on(c) ? c->hid : nullptr,
-                   c->hcnt->ovf_n > 0, c->cnt, c->st, &c->launches));
+                   c->hcnt->ovf_n > 0, false, c->cnt, c->st, &c->launches));
+  c->dip_valid = false;
   // the switch left the FP64 terms of the switching spins in the cache: valid now unless the
   // graph was switched from other spins (the epoch start of a restored checkpoint)
   c->cache_state = src == c->s ? 0 : 2;
@@ -505,6 +508,10 @@ sco_status sco_sweep(sco_ctx* c, int32_t n_mcs) {
 sco_status sco_observables(sco_ctx* c, sco_obs* o, int32_t want_full) {
   if (!c || !o) return SCO_EINVAL;
   const bool full = want_full && c->P.N <= 65536;
+  if (c->graph_epoch >= 0 && !c->dip_valid) {
+    SCO_TRY(dip_degree_run(c->P, c->row_ptr, c->col, c->cnt, c->st, &c->launches));
+    c->dip_valid = true;
+  }
   SCO_TRY(observables_run(c->P, c->s, c->row_ptr, c->col, c->tab.xy, c->graph_epoch >= 0, full,
                           c->cnt, c->st, &c->launches));
   sco_status st = read_counters(c);
@@ -568,9 +575,19 @@ sco_status sco_get_graph(sco_ctx* c, uint32_t* row_ptr, uint32_t* col, uint32_t*
   if (row_ptr)
     SCO_TRY(cudaMemcpyAsync(row_ptr, c->row_ptr, (c->P.N + 1) * sizeof(uint32_t),
                             cudaMemcpyDeviceToHost, c->st));
-  if (col && c->nnz)
-    SCO_TRY(cudaMemcpyAsync(col, c->col, c->nnz * sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                            c->st));
+  if (col && c->nnz) {
+    // the device rows are unsorted: copy, sort every row by neighbour index, then read back
+    uint32_t* tmp = nullptr;
+    SCO_TRY(cudaMalloc(&tmp, c->nnz * sizeof(uint32_t)));
+    cudaError_t e = csr_sorted_copy(c->P, c->row_ptr, c->col, tmp, c->nnz, c->cnt, c->st,
+                                    &c->launches);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(col, tmp, c->nnz * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(tmp);
+    SCO_TRY(e);
+    c->dip_valid = true;
+  }
   if (colour)
     SCO_TRY(cudaMemcpyAsync(colour, c->cb.colour, c->P.N * sizeof(uint32_t),
                             cudaMemcpyDeviceToHost, c->st));

@@ -50,6 +50,9 @@ struct KwView {
   uint32_t* ilist;
   const unsigned* gmax;         // optional: largest palette on the device (else pal)
   uint32_t low_gmax;            // levels 1..kw_low_levels(g, M, low_gmax) done block-locally
+  // buckets of at most this many vertices (record path) run without grid barriers between
+  // them, each item waiting for its listed larger neighbours; 0: a quarter of the grid
+  uint32_t free_max;
 };
 
 constexpr int kItemList = kKwItemList;
@@ -407,13 +410,14 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
         ok = grid_sync(V.bar, V.status, V.ns_limit);
         c = next_bucket(ct);
       }
-      // the buckets below that hold at most a quarter of the grid's threads each run with no
-      // barrier between them: every thread takes their items in descending colour order and
-      // waits (bounded) for the listed neighbours, all of larger colour, hence taken up
-      // earlier by their own threads; one grid barrier publishes the run
+      // the buckets below that hold at most free_max vertices each run with no barrier
+      // between them: every thread takes their items in descending colour order and waits
+      // (bounded) for the listed neighbours, all of larger colour, hence taken up earlier by
+      // their own threads (no cycle of waits); one grid barrier publishes the run
       if (ok && c >= 0) {
         int cm = c;
-        while (cm >= 0 && start[cm + 1] - start[cm] <= nth / 4) --cm;
+        const uint32_t fmax = V.free_max ? V.free_max : nth / 4;
+        while (cm >= 0 && start[cm + 1] - start[cm] <= fmax) --cm;
         if (cm < c) {
           const uint32_t hi = start[c + 1], lo = start[cm + 1];
           bool mine = true;

@@ -64,6 +64,9 @@ cudaError_t spins_init(const DevParams& P, double* s, float4* s32, cudaStream_t 
                        int64_t* launches);
 cudaError_t spins_to_f32(int64_t N, const double* s, float4* s32, cudaStream_t st,
                          int64_t* launches);
+// largest dipolar degree of the current graph into cnt->max_degree_dip
+cudaError_t dip_degree_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
+                           DevCounters* cnt, cudaStream_t st, int64_t* launches);
 cudaError_t observables_run(const DevParams& P, const double* s, const uint32_t* row_ptr,
                             const uint32_t* col, const double2* xy, bool have_graph,
                             bool want_full, DevCounters* cnt, cudaStream_t st, int64_t* launches);
@@ -94,10 +97,18 @@ cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, cons
 cudaError_t csr_scan(const DevParams& P, SwitchBufs& b, uint32_t* row_ptr, DevCounters* cnt,
                      cudaStream_t st, int64_t* launches);
 // hid (optional, parallel to col): the half-edge id of every CSR entry (both entries of a pair
-// carry the id of its half-edge), sorted with its row.
+// carry the id of its half-edge).  sort_rows (only without hid): sort every row by neighbour
+// index and record the largest dipolar degree; else a row holds its lower neighbours in the
+// order of their atomic slots, then its upper ones in switching order (no result depends on
+// the order inside a row).
 cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* row_ptr,
-                     uint32_t* col, uint32_t* hid, bool has_overflow, DevCounters* cnt,
-                     cudaStream_t st, int64_t* launches);
+                     uint32_t* col, uint32_t* hid, bool has_overflow, bool sort_rows,
+                     DevCounters* cnt, cudaStream_t st, int64_t* launches);
+// out = col with every row sorted by neighbour index (the documented layout of the getters);
+// also records the largest dipolar degree in cnt.
+cudaError_t csr_sorted_copy(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
+                            uint32_t* out, uint64_t nnz, DevCounters* cnt, cudaStream_t st,
+                            int64_t* launches);
 
 // ---- colour.cu ----
 struct ColourBufs {

@@ -169,6 +169,28 @@ cudaError_t spins_to_f32(int64_t N, const double* s, float4* s32, cudaStream_t s
   return cudaGetLastError();
 }
 
+// Largest number of dipolar entries (exchange-only bonds excluded) in a row: Table 1's Delta.
+__global__ void k_dip_degree(int64_t N, const uint32_t* __restrict__ row_ptr,
+                             const uint32_t* __restrict__ col, DevCounters* __restrict__ cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned nd = 0;
+  if (i < N)
+    for (uint32_t e = row_ptr[i], e1 = row_ptr[i + 1]; e < e1; ++e)
+      nd += (col[e] & kExchOnly) ? 0u : 1u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nd = max(nd, __shfl_down_sync(0xffffffffu, nd, o));
+  if ((threadIdx.x & 31) == 0 && nd) atomicMax(&cnt->max_degree_dip, nd);
+}
+
+cudaError_t dip_degree_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
+                           DevCounters* cnt, cudaStream_t st, int64_t* launches) {
+  cudaError_t e = cudaMemsetAsync(&cnt->max_degree_dip, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  k_dip_degree<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P.N, row_ptr, col, cnt);
+  ++*launches;
+  return cudaGetLastError();
+}
+
 cudaError_t observables_run(const DevParams& P, const double* s, const uint32_t* row_ptr,
                             const uint32_t* col, const double2* xy, bool have_graph,
                             bool want_full, DevCounters* cnt, cudaStream_t st,

@@ -163,19 +163,6 @@ __global__ void k_rowsort(int64_t N, const uint32_t* __restrict__ row_ptr,
   if ((threadIdx.x & 31) == 0 && nd) atomicMax(&cnt->max_degree_dip, nd);
 }
 
-// The same with the half-edge ids moved along with their entries.
-__global__ void k_rowsort_pay(int64_t N, const uint32_t* __restrict__ row_ptr,
-                              uint32_t* __restrict__ col, uint32_t* __restrict__ hid,
-                              DevCounters* __restrict__ cnt) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  unsigned nd = 0;
-  if (i < N)
-    nd = sort_row_pay(col + row_ptr[i], hid + row_ptr[i], row_ptr[i + 1] - row_ptr[i]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nd = max(nd, __shfl_down_sync(0xffffffffu, nd, o));
-  if ((threadIdx.x & 31) == 0 && nd) atomicMax(&cnt->max_degree_dip, nd);
-}
-
 }  // namespace
 
 cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float4* s32,
@@ -216,8 +203,8 @@ cudaError_t csr_scan(const DevParams& P, SwitchBufs& b, uint32_t* row_ptr, DevCo
 }
 
 cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* row_ptr,
-                     uint32_t* col, uint32_t* hid, bool has_overflow, DevCounters* cnt,
-                     cudaStream_t st, int64_t* launches) {
+                     uint32_t* col, uint32_t* hid, bool has_overflow, bool sort_rows,
+                     DevCounters* cnt, cudaStream_t st, int64_t* launches) {
   cudaError_t e = cudaMemsetAsync(b.lcur, 0, P.N * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((P.N + 255) / 256);
@@ -237,8 +224,20 @@ cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* ro
       ++*launches;
     }
   }
-  if (hid) k_rowsort_pay<<<nb, 256, 0, st>>>(P.N, row_ptr, col, hid, cnt);
-  else k_rowsort<<<nb, 256, 0, st>>>(P.N, row_ptr, col, cnt);
+  if (sort_rows) {  // (the half-edge ids are not moved: callers that keep them leave rows unsorted)
+    if (hid) return cudaErrorInvalidValue;
+    k_rowsort<<<nb, 256, 0, st>>>(P.N, row_ptr, col, cnt);
+    ++*launches;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t csr_sorted_copy(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
+                            uint32_t* out, uint64_t nnz, DevCounters* cnt, cudaStream_t st,
+                            int64_t* launches) {
+  cudaError_t e = cudaMemcpyAsync(out, col, nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  k_rowsort<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P.N, row_ptr, out, cnt);
   ++*launches;
   return cudaGetLastError();
 }

@@ -472,66 +472,5 @@ __device__ __forceinline__ unsigned sort_row(uint32_t* __restrict__ r, uint32_t 
   return nd;
 }
 
-// Compare-exchange on the neighbour index, its payload (pair id) travelling with it.
-__device__ __forceinline__ void row_ce2(uint32_t& a, uint32_t& b, uint32_t& pa, uint32_t& pb) {
-  const bool sw = (a & kIndexMask) > (b & kIndexMask);
-  const uint32_t lo = sw ? b : a, hi = sw ? a : b;
-  const uint32_t plo = sw ? pb : pa, phi = sw ? pa : pb;
-  a = lo;
-  b = hi;
-  pa = plo;
-  pb = phi;
-}
-
-// sort_row with a payload per entry (pe, moved with its entry).
-__device__ __forceinline__ unsigned sort_row_pay(uint32_t* __restrict__ r, uint32_t* __restrict__ pe,
-                                                 uint32_t n) {
-  unsigned nd = 0;
-  if (n <= 32) {
-    uint32_t v[32], w[32];
-#pragma unroll
-    for (int a = 0; a < 32; ++a) {
-      v[a] = (uint32_t)a < n ? r[a] : 0xFFFFFFFFu;
-      w[a] = (uint32_t)a < n ? pe[a] : 0u;
-    }
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-      for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-        for (int a = 0; a < 32; ++a) {
-          const int l = a ^ j;
-          if (l > a) {
-            if ((a & k) == 0) row_ce2(v[a], v[l], w[a], w[l]);
-            else row_ce2(v[l], v[a], w[l], w[a]);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 32; ++a) {
-      if ((uint32_t)a < n) {
-        r[a] = v[a];
-        pe[a] = w[a];
-        nd += (v[a] & kExchOnly) ? 0u : 1u;
-      }
-    }
-  } else {
-    for (uint32_t a = 1; a < n; ++a) {
-      const uint32_t x = r[a], px = pe[a];
-      uint32_t c = a;
-      while (c > 0 && (r[c - 1] & kIndexMask) > (x & kIndexMask)) {
-        r[c] = r[c - 1];
-        pe[c] = pe[c - 1];
-        --c;
-      }
-      r[c] = x;
-      pe[c] = px;
-    }
-    for (uint32_t a = 0; a < n; ++a) nd += (r[a] & kExchOnly) ? 0u : 1u;
-  }
-  return nd;
-}
-
 }  // namespace
 }  // namespace sco
