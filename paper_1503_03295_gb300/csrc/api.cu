@@ -202,22 +202,19 @@ cudaError_t grow(T*& ptr, uint64_t& cap, uint64_t need) {
 
 bool cache_on(const sco_ctx* c) { return c->sw.keep != nullptr; }
 
-// The three per-half-edge arrays of the pair cache for the current overflow capacity.
+// The per-half-edge records of the pair cache for the current overflow capacity.
 cudaError_t alloc_keep(sco_ctx* c) {
   cudaFree(c->sw.keep);
-  cudaFree(c->sw.keep_e);
-  cudaFree(c->sw.keep_l);
-  c->sw.keep = c->sw.keep_e = c->sw.keep_l = nullptr;
+  c->sw.keep = nullptr;
   const size_t n = (size_t)c->P.N * kSlotCap + c->sw.ovf_cap;
-  cudaError_t e = cudaMalloc(&c->sw.keep, n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->sw.keep_e, n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->sw.keep_l, n * sizeof(double));
-  return e;
+  return cudaMalloc(&c->sw.keep, n * sizeof(double4_32a));
 }
 
 PairCache pair_cache(sco_ctx* c) {
   if (!cache_on(c)) return PairCache{};
-  return PairCache{c->hid, c->sw.keep, c->sw.keep_e, c->sw.keep_l, c->upd};
+  // the last endpoint's term is needed only when the next step keeps this graph
+  const int carry = (c->t + 1) % c->p.n_sw != 0 ? 1 : 0;
+  return PairCache{c->hid, c->sw.keep, c->upd, carry};
 }
 
 sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4* src32) {
@@ -246,9 +243,7 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4
       // half-edge ids must stay below 2^32 for the cache: else run without it
       if ((uint64_t)c->P.N * kSlotCap + need >= (1ull << 32)) {
         cudaFree(c->sw.keep);
-        cudaFree(c->sw.keep_e);
-        cudaFree(c->sw.keep_l);
-        c->sw.keep = c->sw.keep_e = c->sw.keep_l = nullptr;
+        c->sw.keep = nullptr;
       } else {
         SCO_TRY(alloc_keep(c));
       }
@@ -340,8 +335,6 @@ void free_all(sco_ctx* c) {
   cudaFree(c->sw.ovf);
   cudaFree(c->sw.scan_tmp);
   cudaFree(c->sw.keep);
-  cudaFree(c->sw.keep_e);
-  cudaFree(c->sw.keep_l);
   cudaFree(c->hid);
   cudaFree(c->upd);
   cudaFree(c->row_ptr);

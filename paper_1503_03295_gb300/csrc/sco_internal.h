@@ -83,13 +83,12 @@ struct SwitchBufs {
   uint32_t* ovf;    // 2 * ovf_cap (i, j | flag)
   uint32_t ovf_cap;
   uint64_t* scan_tmp;
-  // FP64 form only (else null): the pair cache, one value per half-edge id h (slot i * kSlotCap
-  // + q of site i, then N * kSlotCap + overflow index): keep = 1 - P_ij at the current spins,
-  // keep_e / keep_l = the same after the move of the endpoint that is updated first / last in
-  // the MC step (written by that endpoint whatever its decision).  N * kSlotCap + ovf_cap each.
-  double* keep;
-  double* keep_e;
-  double* keep_l;
+  // FP64 form only (else null): the pair cache, one 32-byte record per half-edge id h (slot
+  // i * kSlotCap + q of site i, then N * kSlotCap + overflow index), N * kSlotCap + ovf_cap of
+  // them: x = 1 - P_ij at the current spins, y / z = the same after the move of the endpoint
+  // that is decided first / last in the MC step (written by that endpoint whatever its
+  // decision), so that every access of a pair touches one sector.
+  double4_32a* keep;
 };
 cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float4* s32,
                        int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,
@@ -142,10 +141,10 @@ cudaError_t bucket_run(const DevParams& P, uint32_t g, const uint32_t* row_ptr, 
 // The FP64 form's pair cache (see sweep_dev.cuh); hid null: no cache.
 struct PairCache {
   const uint32_t* hid;  // per CSR entry: half-edge id of its pair
-  double* keep;         // per half-edge: 1 - P_ij at the MC step's start spins
-  double* keep_e;       // ... after the move of the endpoint decided first in the step
-  double* keep_l;       // ... after the move of the endpoint decided last
+  double4_32a* keep;    // per half-edge: {1 - P_ij at the step's start spins, after the move of
+                        //  the endpoint decided first, after the move of the one decided last}
   uint8_t* upd;         // per site in this MC step: 0 not decided, 1 rejected, 2 accepted
+  int carry;            // the next step uses this graph again: the last endpoint writes z too
 };
 cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,

@@ -143,33 +143,30 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
 }
 
 // Pair cache between two MC steps on the same graph: the term of every pair at the current
-// spins is keep_l (the later endpoint moved), else keep_e (only the earlier one moved), else the
-// unchanged keep.  One thread per site over its half-edges (slots), then the overflow list.
+// spins is the record's z (the later endpoint moved), else its y (only the earlier one moved),
+// else the unchanged x.  One thread per site over its half-edges (slots), then the overflow list.
 __device__ __forceinline__ void cache_carry(uint32_t i, uint32_t jv, uint32_t h,
                                             const uint32_t* __restrict__ colour,
-                                            const uint8_t* __restrict__ upd, double* keep,
-                                            const double* __restrict__ keep_e,
-                                            const double* __restrict__ keep_l) {
+                                            const uint8_t* __restrict__ upd, double4_32a* keep) {
   if (jv & kExchOnly) return;
   const uint32_t j = jv & kIndexMask;
   const bool i_first = colour[i] < colour[j];
   const uint32_t ue = upd[i_first ? i : j], ul = upd[i_first ? j : i];
-  if (ul == 2u) keep[h] = keep_l[h];
-  else if (ue == 2u) keep[h] = keep_e[h];
+  if (ul == 2u) keep[h].x = keep[h].z;
+  else if (ue == 2u) keep[h].x = keep[h].y;
 }
 
 __global__ void __launch_bounds__(256) k_cache_carry(int64_t N, const uint32_t* __restrict__ hslot,
                                                      const uint32_t* __restrict__ hcnt,
                                                      const uint32_t* __restrict__ colour,
-                                                     const uint8_t* __restrict__ upd, double* keep,
-                                                     const double* __restrict__ keep_e,
-                                                     const double* __restrict__ keep_l) {
+                                                     const uint8_t* __restrict__ upd,
+                                                     double4_32a* keep) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint32_t n = min(hcnt[i], (uint32_t)kSlotCap);
   for (uint32_t q = 0; q < n; ++q) {
     const uint32_t h = (uint32_t)i * (uint32_t)kSlotCap + q;
-    cache_carry((uint32_t)i, hslot[h], h, colour, upd, keep, keep_e, keep_l);
+    cache_carry((uint32_t)i, hslot[h], h, colour, upd, keep);
   }
 }
 
@@ -178,21 +175,18 @@ __global__ void __launch_bounds__(256) k_cache_carry_ovf(uint32_t N, const uint3
                                                          uint32_t ovf_cap,
                                                          const uint32_t* __restrict__ colour,
                                                          const uint8_t* __restrict__ upd,
-                                                         double* keep,
-                                                         const double* __restrict__ keep_e,
-                                                         const double* __restrict__ keep_l) {
+                                                         double4_32a* keep) {
   const unsigned long long n = min(cnt->ovf_n, (unsigned long long)ovf_cap);
   for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
        q += (unsigned long long)gridDim.x * blockDim.x)
-    cache_carry(ovf[2 * q], ovf[2 * q + 1], N * (uint32_t)kSlotCap + (uint32_t)q, colour, upd, keep,
-                keep_e, keep_l);
+    cache_carry(ovf[2 * q], ovf[2 * q + 1], N * (uint32_t)kSlotCap + (uint32_t)q, colour, upd, keep);
 }
 
 // Pair cache from scratch at the current spins (after the spins changed outside the sweep): the
 // FP64 term of every surviving dipolar pair, evaluated as the switch does.
 __device__ __forceinline__ void cache_build(const DevParams& P, const Sw64* __restrict__ sw,
                                             const double* __restrict__ s, uint32_t i, uint32_t jv,
-                                            uint32_t h, double* keep) {
+                                            uint32_t h, double4_32a* keep) {
   if (jv & kExchOnly) return;
   const uint32_t j = jv & kIndexMask;
   const uint32_t yi = site_row(i, P), yj = site_row(j, P);
@@ -200,8 +194,8 @@ __device__ __forceinline__ void cache_build(const DevParams& P, const Sw64* __re
   const int32_t dy = (int32_t)yj - (int32_t)yi;
   const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
   const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-  keep[h] = pair_keep64(sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)], Si,
-                        Sj, dx, dy);
+  keep[h].x = pair_keep64(sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)],
+                          Si, Sj, dx, dy);
 }
 
 __global__ void __launch_bounds__(256) k_cache_build(const DevParams P, const Sw64* __restrict__ sw,
@@ -210,7 +204,7 @@ __global__ void __launch_bounds__(256) k_cache_build(const DevParams P, const Sw
                                                      const uint32_t* __restrict__ hcnt,
                                                      const uint32_t* __restrict__ ovf,
                                                      const DevCounters* __restrict__ cnt,
-                                                     uint32_t ovf_cap, double* keep) {
+                                                     uint32_t ovf_cap, double4_32a* keep) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < P.N) {
     const uint32_t n = min(hcnt[i], (uint32_t)kSlotCap);
@@ -232,9 +226,9 @@ cudaError_t cache_carry_run(const DevParams& P, const SwitchBufs& b, const uint3
                             const uint8_t* upd, const DevCounters* cnt, cudaStream_t st,
                             int64_t* launches) {
   const unsigned nb = (unsigned)((P.N + 255) / 256);
-  k_cache_carry<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, colour, upd, b.keep, b.keep_e, b.keep_l);
-  k_cache_carry_ovf<<<(unsigned)(2 * num_sms()), 256, 0, st>>>(
-      (uint32_t)P.N, b.ovf, cnt, b.ovf_cap, colour, upd, b.keep, b.keep_e, b.keep_l);
+  k_cache_carry<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, colour, upd, b.keep);
+  k_cache_carry_ovf<<<(unsigned)(2 * num_sms()), 256, 0, st>>>((uint32_t)P.N, b.ovf, cnt,
+                                                               b.ovf_cap, colour, upd, b.keep);
   *launches += 2;
   return cudaGetLastError();
 }

@@ -256,8 +256,8 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
 // Where a site writes its upper neighbours: kSlotCap slots of its own (row `id` of hslot), then
 // an overflow list shared by all sites (entry: site id, j | flag).  indeg counts lower
 // neighbours per (local) site.  keep / keep_ovf (optional, FP64 form): the FP64 value of
-// 1 - P_ij of each surviving dipolar pair, at the same slot or overflow index (the pair cache
-// that the FP64 sweep starts from).
+// 1 - P_ij of each surviving dipolar pair, written to the x field of the pair-cache record at
+// the same slot or overflow index (the cache that the FP64 sweep starts from).
 struct SwitchOut {
   uint32_t* hslot;
   uint32_t* indeg;
@@ -265,8 +265,8 @@ struct SwitchOut {
   uint32_t ovf_cap;
   unsigned long long* ovf_n;
   int* status;
-  double* keep = nullptr;
-  double* keep_ovf = nullptr;
+  double4_32a* keep = nullptr;
+  double4_32a* keep_ovf = nullptr;
 };
 
 // One site's walk along its half-plane list: the candidate search of Sec. 2.1 with the state it
@@ -291,13 +291,13 @@ __device__ __forceinline__ void switch_emit(const SwitchOut& o, uint32_t id, uin
                                             uint32_t jv, double keep = 0.0) {
   if (n_out < (uint32_t)kSlotCap) {
     o.hslot[(size_t)id * kSlotCap + n_out] = jv;
-    if (o.keep) o.keep[(size_t)id * kSlotCap + n_out] = keep;
+    if (o.keep) o.keep[(size_t)id * kSlotCap + n_out].x = keep;
   } else {
     const unsigned long long idx = atomicAdd(o.ovf_n, 1ull);
     if (idx < o.ovf_cap) {
       o.ovf[2 * idx] = id;
       o.ovf[2 * idx + 1] = jv;
-      if (o.keep) o.keep_ovf[idx] = keep;
+      if (o.keep) o.keep_ovf[idx].x = keep;
     } else {
       set_status(o.status, kStatusCapacity);
     }
