@@ -239,6 +239,9 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4
     c->sw.ovf = nullptr;
     SCO_TRY(cudaMalloc(&c->sw.ovf, 2 * need * sizeof(uint32_t)));
     c->sw.ovf_cap = (uint32_t)need;
+    cudaFree(c->sw.rank);
+    c->sw.rank = nullptr;
+    SCO_TRY(cudaMalloc(&c->sw.rank, ((size_t)c->P.N * kSlotCap + need) * sizeof(uint32_t)));
     if (cache_on(c)) {
       // half-edge ids must stay below 2^32 for the cache: else run without it
       if ((uint64_t)c->P.N * kSlotCap + need >= (1ull << 32)) {
@@ -335,6 +338,7 @@ void free_all(sco_ctx* c) {
   cudaFree(c->sw.ovf);
   cudaFree(c->sw.scan_tmp);
   cudaFree(c->sw.keep);
+  cudaFree(c->sw.rank);
   cudaFree(c->hid);
   cudaFree(c->upd);
   cudaFree(c->row_ptr);
@@ -433,6 +437,9 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (e == cudaSuccess) e = cudaMallocHost(&c->hcnt, sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, sizeof(DevCounters), c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, N, c->st);
+  if (e != cudaSuccess) return fail(from_cuda(e));
+  // the switch's ticket per half-edge (places the lower CSR entries without atomics)
+  e = cudaMalloc(&c->sw.rank, ((size_t)N * kSlotCap + c->sw.ovf_cap) * sizeof(uint32_t));
   if (e != cudaSuccess) return fail(from_cuda(e));
   // the FP64 form keeps the pair cache while half-edge ids fit 32 bits
   if (p->precision == SCO_FP64 && (uint64_t)N * kSlotCap + c->sw.ovf_cap < (1ull << 32)) {

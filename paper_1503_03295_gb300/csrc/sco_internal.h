@@ -89,6 +89,9 @@ struct SwitchBufs {
   // that is decided first / last in the MC step (written by that endpoint whatever its
   // decision), so that every access of a pair touches one sector.
   double4_32a* keep;
+  // per half-edge id (as keep): its rank among the lower neighbours of its upper site, from the
+  // switch's atomic on indeg (null: k_fill takes its own)
+  uint32_t* rank;
 };
 cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float4* s32,
                        int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,

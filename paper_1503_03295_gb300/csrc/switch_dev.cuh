@@ -58,7 +58,8 @@ struct NearTable {
 };
 
 // Exact re-evaluation of the next candidate: min { k > s : beta D 2^-58 (W_k - W_s) >= -ln u+ }.
-__device__ __noinline__ int64_t next_candidate_dd(const DevParams& P, const NearTable& T,
+// The table view comes by value (its address would put the caller's copy in local memory).
+__device__ __noinline__ int64_t next_candidate_dd(const DevParams& P, const NearTable T,
                                                   int64_t s, uint64_t Ws, double up) {
   const dd ln2 = {P.ln2_hi, P.ln2_lo};
   const dd E = dd_neg(dd_log(dd_from(up), ln2));
@@ -169,9 +170,13 @@ __device__ __forceinline__ int64_t next_candidate_fp32(const DevParams& P, const
   return next_candidate(P, T, s, Ws, Wtot, wE, ghits);
 }
 
-// Exact survival test u q < 1 - P_ij in double-double.
-__device__ __noinline__ bool survives_dd(const DevParams& P, const double* Si, const double* Sj,
-                                         int32_t dx, int32_t dy, uint64_t A, double u1) {
+// Exact survival test u q < 1 - P_ij in double-double.  The spins come by value, so that the
+// callers' spin copies stay in registers (an address passed to a function that is not inlined
+// would put them in local memory on the fast path too).
+__device__ __noinline__ bool survives_dd(const DevParams& P, double si0, double si1, double si2,
+                                         double sj0, double sj1, double sj2, int32_t dx,
+                                         int32_t dy, uint64_t A, double u1) {
+  const double Si[3] = {si0, si1, si2}, Sj[3] = {sj0, sj1, sj2};
   const dd ln2 = {P.ln2_hi, P.ln2_lo};
   const int64_t r2 = (int64_t)dx * dx + (int64_t)dy * dy;
   const dd V = dd_pair_V(P.D, coupling_c(r2), (double)r2, Si, Sj, (double)dx, (double)dy);
@@ -213,7 +218,7 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t,
   if (om > ob) return true;
   if (om < -ob - 1) return false;
   ++ghits;
-  return survives_dd(P, Si, Sj, dx, dy, A, u1);
+  return survives_dd(P, Si[0], Si[1], Si[2], Sj[0], Sj[1], Sj[2], dx, dy, A, u1);
 }
 
 // FP32 screen of the same test (FP32-guarded form): spins from the FP32 shadow
@@ -267,6 +272,11 @@ struct SwitchOut {
   int* status;
   double4_32a* keep = nullptr;
   double4_32a* keep_ovf = nullptr;
+  // rank / rank_ovf (optional): the half-edge's ticket among the lower neighbours of j (the
+  // value its atomic on indeg[j] returned), which places the pair in j's row without a second
+  // atomic
+  uint32_t* rank = nullptr;
+  uint32_t* rank_ovf = nullptr;
 };
 
 // One site's walk along its half-plane list: the candidate search of Sec. 2.1 with the state it
@@ -289,21 +299,23 @@ struct SiteWalk {
 
 __device__ __forceinline__ void switch_emit(const SwitchOut& o, uint32_t id, uint32_t& n_out,
                                             uint32_t jv, double keep = 0.0) {
+  const uint32_t rk = atomicAdd(&o.indeg[jv & kIndexMask], 1u);
   if (n_out < (uint32_t)kSlotCap) {
     o.hslot[(size_t)id * kSlotCap + n_out] = jv;
     if (o.keep) o.keep[(size_t)id * kSlotCap + n_out].x = keep;
+    if (o.rank) o.rank[(size_t)id * kSlotCap + n_out] = rk;
   } else {
     const unsigned long long idx = atomicAdd(o.ovf_n, 1ull);
     if (idx < o.ovf_cap) {
       o.ovf[2 * idx] = id;
       o.ovf[2 * idx + 1] = jv;
       if (o.keep) o.keep_ovf[idx].x = keep;
+      if (o.rank) o.rank_ovf[idx] = rk;
     } else {
       set_status(o.status, kStatusCapacity);
     }
   }
   ++n_out;
-  atomicAdd(&o.indeg[jv & kIndexMask], 1u);
 }
 
 template <int PREC>

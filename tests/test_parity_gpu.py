@@ -200,7 +200,15 @@ def test_full_size_first_sweep_L2304():
     assert np.array_equal(g.spins(), o.spins())
     og, oo = g.observables(), o.observables()
     assert og["kw_rounds"] == oo["kw_rounds"]
+    assert og["max_degree_dipolar"] == oo["max_degree_dipolar"]
     _same_energy(og["e_switched"], oo["e_switched"], g.N)
+    # the graph diagnostics at full size, for the processor counts of Fig. 6
+    for cx, cy in ((6, 8), (16, 18)):
+        a, b = g.graph_stats(cx, cy, 64), o.graph_stats(cx, cy, 64)
+        assert a["n_cross"] == b["n_cross"] and np.array_equal(a["survived"], b["survived"])
+        assert np.array_equal(a["pairs"], b["pairs"])
+        assert a["delta_r_weighted"] == b["delta_r_weighted"]
+        assert np.array_equal(a["delta_r"], b["delta_r"], equal_nan=True)
     g.close()
     g32 = sco.Lattice(sco.make_params(2304, T=0.6, seed=0, precision=sco.FP32_GUARDED))
     g32.sweep(1)
