@@ -179,8 +179,8 @@ FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal: context
 # FP64 sweep kernels, per pair of the switched graph and per spin update, from one ncu capture
 # of the current kernels on a smaller lattice at T = 0.6 D (DRAM bytes and executed FP64
 # thread-instructions scale with the updates and pairs, not with L): see the named profile
-SWEEP64_EXECUTED_FP64_PER_PAIR = None
-SWEEP64_DRAM_BYTES_PER_UPDATE = None
+SWEEP64_EXECUTED_FP64_PER_PAIR = 42.9  # k_propose + k_sweep + k_resolve, thread-instructions
+SWEEP64_DRAM_BYTES_PER_UPDATE = 2656.0  # dram__bytes_read.sum + dram__bytes_write.sum
 SWEEP64_TRAFFIC_T = 0.6
 SWEEP64_EXECUTED_SOURCE = "profiles/k_sweep_fp64_L1024_T0.6.md"
 
@@ -217,11 +217,13 @@ def algorithmic_bytes(k, M, p0):
 
 def algorithmic_flops(k, cand):
     """FP64 operations per spin update of the FP64 form, planning figures: 70 per switching
-    candidate (one logarithm, one expm1, the pair energy) and 120 per pair of the sweep
-    (two pair energies, two pseudointeraction terms, a log1mexp counted as two
-    transcendentals); the colouring has none.  The kernels issue fewer (about 40 per candidate
-    and 39 per pair), so these fractions measure work done against the plan."""
-    return {"switch": 70.0 * cand, "colour": 0.0, "sweep": 120.0 * k}
+    candidate (one logarithm, one expm1, the pair energy) and, per pair endpoint of the sweep,
+    two pair energies (20) and the pseudointeraction term of the proposed spin (50, a log1mexp
+    counted as two transcendentals): the old spin's term is read from the pair cache, which the
+    switch filled, so 70 (120 without the cache); the colouring has none.  The kernels issue
+    fewer (about 40 per candidate, 43 per pair endpoint: see SWEEP64_EXECUTED_FP64_PER_PAIR), so
+    these fractions measure work done against the plan."""
+    return {"switch": 70.0 * cand, "colour": 0.0, "sweep": 70.0 * k}
 
 
 def phase_ms(ph):

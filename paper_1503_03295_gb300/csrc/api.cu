@@ -205,16 +205,21 @@ bool cache_on(const sco_ctx* c) { return c->sw.keep != nullptr; }
 // The per-half-edge records of the pair cache for the current overflow capacity.
 cudaError_t alloc_keep(sco_ctx* c) {
   cudaFree(c->sw.keep);
+  cudaFree(c->sw.keepl);
   c->sw.keep = nullptr;
+  c->sw.keepl = nullptr;
   const size_t n = (size_t)c->P.N * kSlotCap + c->sw.ovf_cap;
-  return cudaMalloc(&c->sw.keep, n * sizeof(double4_32a));
+  cudaError_t e = cudaMalloc(&c->sw.keep, n * sizeof(double4_32a));
+  // the last endpoint's values are kept only when a graph serves several steps
+  if (e == cudaSuccess && c->p.n_sw > 1) e = cudaMalloc(&c->sw.keepl, n * sizeof(double2));
+  return e;
 }
 
 PairCache pair_cache(sco_ctx* c) {
   if (!cache_on(c)) return PairCache{};
   // the last endpoint's term is needed only when the next step keeps this graph
   const int carry = (c->t + 1) % c->p.n_sw != 0 ? 1 : 0;
-  return PairCache{c->hid, c->sw.keep, c->upd, carry};
+  return PairCache{c->hid, c->sw.keep, c->sw.keepl, c->upd, carry && c->sw.keepl ? 1 : 0};
 }
 
 sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4* src32) {
@@ -239,14 +244,13 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4
     c->sw.ovf = nullptr;
     SCO_TRY(cudaMalloc(&c->sw.ovf, 2 * need * sizeof(uint32_t)));
     c->sw.ovf_cap = (uint32_t)need;
-    cudaFree(c->sw.rank);
-    c->sw.rank = nullptr;
-    SCO_TRY(cudaMalloc(&c->sw.rank, ((size_t)c->P.N * kSlotCap + need) * sizeof(uint32_t)));
     if (cache_on(c)) {
       // half-edge ids must stay below 2^32 for the cache: else run without it
       if ((uint64_t)c->P.N * kSlotCap + need >= (1ull << 32)) {
         cudaFree(c->sw.keep);
+        cudaFree(c->sw.keepl);
         c->sw.keep = nullptr;
+        c->sw.keepl = nullptr;
       } else {
         SCO_TRY(alloc_keep(c));
       }
@@ -338,7 +342,7 @@ void free_all(sco_ctx* c) {
   cudaFree(c->sw.ovf);
   cudaFree(c->sw.scan_tmp);
   cudaFree(c->sw.keep);
-  cudaFree(c->sw.rank);
+  cudaFree(c->sw.keepl);
   cudaFree(c->hid);
   cudaFree(c->upd);
   cudaFree(c->row_ptr);
@@ -437,9 +441,6 @@ sco_status sco_init(const sco_params* p, void* stream, sco_ctx** out) {
   if (e == cudaSuccess) e = cudaMallocHost(&c->hcnt, sizeof(DevCounters));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, sizeof(DevCounters), c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, N, c->st);
-  if (e != cudaSuccess) return fail(from_cuda(e));
-  // the switch's ticket per half-edge (places the lower CSR entries without atomics)
-  e = cudaMalloc(&c->sw.rank, ((size_t)N * kSlotCap + c->sw.ovf_cap) * sizeof(uint32_t));
   if (e != cudaSuccess) return fail(from_cuda(e));
   // the FP64 form keeps the pair cache while half-edge ids fit 32 bits
   if (p->precision == SCO_FP64 && (uint64_t)N * kSlotCap + c->sw.ovf_cap < (1ull << 32)) {

@@ -85,13 +85,12 @@ struct SwitchBufs {
   uint64_t* scan_tmp;
   // FP64 form only (else null): the pair cache, one 32-byte record per half-edge id h (slot
   // i * kSlotCap + q of site i, then N * kSlotCap + overflow index), N * kSlotCap + ovf_cap of
-  // them: x = 1 - P_ij at the current spins, y / z = the same after the move of the endpoint
-  // that is decided first / last in the MC step (written by that endpoint whatever its
-  // decision), so that every access of a pair touches one sector.
+  // them: {1 - P_ij, x = beta (V - Vmax)} at the current spins, then the same two after the
+  // move of the endpoint that is decided first in the MC step (written by that endpoint
+  // whatever its decision), so that every access of a pair touches one sector; keepl (when the
+  // graph serves several steps): the same two after the move of the endpoint decided last.
   double4_32a* keep;
-  // per half-edge id (as keep): its rank among the lower neighbours of its upper site, from the
-  // switch's atomic on indeg (null: k_fill takes its own)
-  uint32_t* rank;
+  double2* keepl;
 };
 cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float4* s32,
                        int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,
@@ -144,10 +143,11 @@ cudaError_t bucket_run(const DevParams& P, uint32_t g, const uint32_t* row_ptr, 
 // The FP64 form's pair cache (see sweep_dev.cuh); hid null: no cache.
 struct PairCache {
   const uint32_t* hid;  // per CSR entry: half-edge id of its pair
-  double4_32a* keep;    // per half-edge: {1 - P_ij at the step's start spins, after the move of
-                        //  the endpoint decided first, after the move of the one decided last}
+  double4_32a* keep;    // per half-edge: {1 - P_ij, x} at the step's start spins, then the two
+                        // after the move of the endpoint decided first
+  double2* keepl;       // per half-edge: {1 - P_ij, x} after the move of the one decided last
   uint8_t* upd;         // per site in this MC step: 0 not decided, 1 rejected, 2 accepted
-  int carry;            // the next step uses this graph again: the last endpoint writes z too
+  int carry;            // the next step uses this graph again: the last endpoint writes keepl
 };
 cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,

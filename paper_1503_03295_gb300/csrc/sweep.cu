@@ -142,31 +142,35 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
   if (lane == 0 && ndd && (fp32_screened || whole)) atomicAdd(&cnt->guard_fp64, ndd);
 }
 
-// Pair cache between two MC steps on the same graph: the term of every pair at the current
-// spins is the record's z (the later endpoint moved), else its y (only the earlier one moved),
-// else the unchanged x.  One thread per site over its half-edges (slots), then the overflow list.
+// Pair cache between two MC steps on the same graph: the values of every pair at the current
+// spins are keepl (the later endpoint moved), else the record's second half (only the earlier
+// one moved), else its unchanged first half.  One thread per site over its half-edges (slots),
+// then the overflow list.
 __device__ __forceinline__ void cache_carry(uint32_t i, uint32_t jv, uint32_t h,
                                             const uint32_t* __restrict__ colour,
-                                            const uint8_t* __restrict__ upd, double4_32a* keep) {
+                                            const uint8_t* __restrict__ upd, double4_32a* keep,
+                                            const double2* __restrict__ keepl) {
   if (jv & kExchOnly) return;
   const uint32_t j = jv & kIndexMask;
   const bool i_first = colour[i] < colour[j];
   const uint32_t ue = upd[i_first ? i : j], ul = upd[i_first ? j : i];
-  if (ul == 2u) keep[h].x = keep[h].z;
-  else if (ue == 2u) keep[h].x = keep[h].y;
+  double2* r = reinterpret_cast<double2*>(&keep[h]);
+  if (ul == 2u) r[0] = keepl[h];
+  else if (ue == 2u) r[0] = r[1];
 }
 
 __global__ void __launch_bounds__(256) k_cache_carry(int64_t N, const uint32_t* __restrict__ hslot,
                                                      const uint32_t* __restrict__ hcnt,
                                                      const uint32_t* __restrict__ colour,
                                                      const uint8_t* __restrict__ upd,
-                                                     double4_32a* keep) {
+                                                     double4_32a* keep,
+                                                     const double2* __restrict__ keepl) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint32_t n = min(hcnt[i], (uint32_t)kSlotCap);
   for (uint32_t q = 0; q < n; ++q) {
     const uint32_t h = (uint32_t)i * (uint32_t)kSlotCap + q;
-    cache_carry((uint32_t)i, hslot[h], h, colour, upd, keep);
+    cache_carry((uint32_t)i, hslot[h], h, colour, upd, keep, keepl);
   }
 }
 
@@ -175,11 +179,13 @@ __global__ void __launch_bounds__(256) k_cache_carry_ovf(uint32_t N, const uint3
                                                          uint32_t ovf_cap,
                                                          const uint32_t* __restrict__ colour,
                                                          const uint8_t* __restrict__ upd,
-                                                         double4_32a* keep) {
+                                                         double4_32a* keep,
+                                                         const double2* __restrict__ keepl) {
   const unsigned long long n = min(cnt->ovf_n, (unsigned long long)ovf_cap);
   for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
        q += (unsigned long long)gridDim.x * blockDim.x)
-    cache_carry(ovf[2 * q], ovf[2 * q + 1], N * (uint32_t)kSlotCap + (uint32_t)q, colour, upd, keep);
+    cache_carry(ovf[2 * q], ovf[2 * q + 1], N * (uint32_t)kSlotCap + (uint32_t)q, colour, upd, keep,
+                keepl);
 }
 
 // Pair cache from scratch at the current spins (after the spins changed outside the sweep): the
@@ -194,8 +200,10 @@ __device__ __forceinline__ void cache_build(const DevParams& P, const Sw64* __re
   const int32_t dy = (int32_t)yj - (int32_t)yi;
   const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
   const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-  keep[h].x = pair_keep64(sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)],
-                          Si, Sj, dx, dy);
+  double x;
+  const double z = pair_keep64(
+      sw[(int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy)], Si, Sj, dx, dy, &x);
+  reinterpret_cast<double2*>(&keep[h])[0] = make_double2(z, x);
 }
 
 __global__ void __launch_bounds__(256) k_cache_build(const DevParams P, const Sw64* __restrict__ sw,
@@ -226,9 +234,9 @@ cudaError_t cache_carry_run(const DevParams& P, const SwitchBufs& b, const uint3
                             const uint8_t* upd, const DevCounters* cnt, cudaStream_t st,
                             int64_t* launches) {
   const unsigned nb = (unsigned)((P.N + 255) / 256);
-  k_cache_carry<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, colour, upd, b.keep);
-  k_cache_carry_ovf<<<(unsigned)(2 * num_sms()), 256, 0, st>>>((uint32_t)P.N, b.ovf, cnt,
-                                                               b.ovf_cap, colour, upd, b.keep);
+  k_cache_carry<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, colour, upd, b.keep, b.keepl);
+  k_cache_carry_ovf<<<(unsigned)(2 * num_sms()), 256, 0, st>>>(
+      (uint32_t)P.N, b.ovf, cnt, b.ovf_cap, colour, upd, b.keep, b.keepl);
   *launches += 2;
   return cudaGetLastError();
 }

@@ -130,17 +130,18 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
 }
 
 // The pair cache of the FP64 form (single lattice).  For every surviving dipolar pair (half-edge
-// id h, carried by both CSR entries of the pair) keep[h].x holds 1 - P = -expm1(x) of the pair
-// at the spins of the MC step's start (the switch leaves its FP64 value there), with the error
-// of any FP64 evaluation of that term (|x error| <= c0 + 2^-52 |x|, relative error of the
-// elementary function within kExpm1RelErr6).  While a site is decided it writes the term at its
-// proposed spin: into keep[h].y when the other endpoint comes later in the step, into
-// keep[h].z (only when the graph serves the next step too) when it came earlier; upd[i] records
-// that site i is done (1 rejected, 2 accepted).  So the old-spin term of a pair is keep[h].x,
-// or keep[h].y when the earlier endpoint moved: one of the two expm1 evaluations per pair is
-// read instead of computed.  A written value <= 0 (the proposed x not strictly negative in
-// FP64) makes every reader leave its decision to the double-double path, which does not use
-// the cache.
+// id h, carried by both CSR entries of the pair) the first half of record keep[h] holds
+// {1 - P = -expm1(x), x = beta (V - Vmax)} of the pair at the spins of the MC step's start (the
+// switch leaves its FP64 values there), each with the error of any FP64 evaluation of it
+// (|x error| <= c0 + 2^-52 |x|, relative error of the elementary function within
+// kExpm1RelErr6).  While a site is decided it writes the pair at its proposed spin: into the
+// record's second half when the other endpoint comes later in the step, into keepl[h] (only
+// when the graph serves the next step too) when it came earlier; upd[i] records that site i is
+// done (1 rejected, 2 accepted).  So the old-spin pair values are the record's first half, or
+// its second half when the earlier endpoint moved: one of the two expm1 evaluations and one of
+// the two dot products per pair endpoint are read instead of computed.  A written 1 - P <= 0
+// (the proposed x not strictly negative in FP64) makes every reader leave its decision to the
+// double-double path, which does not use the cache.
 // accept_fp64 with the old-spin terms from the pair cache; writes the proposed-spin term of
 // every pair (the loop visits every pair, also when the decision is already undecided).
 __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const SiteCtx& c,
@@ -172,18 +173,18 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
     const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
     const double a1 = t.a1, bvm = t.bvm;
     const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
-    const double2 kv = *reinterpret_cast<const double2*>(&pc.keep[h]);  // one sector
-    const double zo = uj == 2u ? kv.y : kv.x;
+    // {1 - P, x} of the pair at the old spin: one 16-byte read of the record's sector
+    const double2 kv = reinterpret_cast<const double2*>(&pc.keep[h])[uj == 2u ? 1 : 0];
+    const double zo = kv.x, xo = kv.y;
     const double tp = bx * ax3 + by * ay3;
     const double gx = a1 * bx - tp * fx;
     const double gy = a1 * by - tp * fy;
     const double gz = a1 * bz;
     const double xn = fma(N0, gx, fma(N1, gy, fma(N2, gz, -bvm)));
-    const double xo = fma(S0, gx, fma(S1, gy, fma(S2, gz, -bvm)));
     const bool okn = neg_strict(xn);
     const double zn = okn ? -expm1_np6(xn) : -1.0;
-    if (uj == 0u) pc.keep[h].y = zn;
-    else if (pc.carry) pc.keep[h].z = zn;
+    if (uj == 0u) reinterpret_cast<double2*>(&pc.keep[h])[1] = make_double2(zn, xn);
+    else if (pc.carry) pc.keepl[h] = make_double2(zn, xn);
     // the cached term must be a positive number (a non-positive one marks an FP64 evaluation
     // that could not be trusted)
     if (!okn || !neg_strict(xo) || !(pos_bits(zo) - 1ull < 0x7FEFFFFFFFFFFFFFull)) {
@@ -503,18 +504,17 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
     const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
     const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
     const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
-    const double2 kv = *reinterpret_cast<const double2*>(&pc.keep[h]);
-    const double zo = uj == 2u ? kv.y : kv.x;
+    const double2 kv = reinterpret_cast<const double2*>(&pc.keep[h])[uj == 2u ? 1 : 0];
+    const double zo = kv.x, xo = kv.y;
     const double tp = bx * ax3 + by * ay3;
     const double gx = t.a1 * bx - tp * fx;
     const double gy = t.a1 * by - tp * fy;
     const double gz = t.a1 * bz;
     const double xn = fma(c.Sn[0], gx, fma(c.Sn[1], gy, fma(c.Sn[2], gz, -t.bvm)));
-    const double xo = fma(c.S[0], gx, fma(c.S[1], gy, fma(c.S[2], gz, -t.bvm)));
     const bool okn = neg_strict(xn);
     const double zn = okn ? -expm1_np6(xn) : -1.0;
-    if (uj == 0u) pc.keep[h].y = zn;
-    else if (pc.carry) pc.keep[h].z = zn;
+    if (uj == 0u) reinterpret_cast<double2*>(&pc.keep[h])[1] = make_double2(zn, xn);
+    else if (pc.carry) pc.keepl[h] = make_double2(zn, xn);
     if (!okn || !neg_strict(xo) || !(pos_bits(zo) - 1ull < 0x7FEFFFFFFFFFFFFFull)) {
       bad = 1;
       continue;

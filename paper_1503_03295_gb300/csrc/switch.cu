@@ -39,10 +39,6 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 5 : 4) k_switch(const DevPara
     o.keep = b.keep;
     o.keep_ovf = b.keep + (size_t)P.N * kSlotCap;
   }
-  if (b.rank) {
-    o.rank = b.rank;
-    o.rank_ovf = b.rank + (size_t)P.N * kSlotCap;
-  }
   const uint32_t N = (uint32_t)P.N;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned below = (1u << lane) - 1u;
@@ -113,13 +109,11 @@ __global__ void k_degree(int64_t N, const uint32_t* __restrict__ hcnt,
 
 // Row i holds its lower neighbours (j < i, scattered here by the sites j) followed by its
 // upper neighbours (written by site i from its slots).  Rows are sorted afterwards.
-// hid (optional): both entries of a pair get the half-edge id i * kSlotCap + q.  rank
-// (optional): the lower entry's place in row j, recorded by the switch (else an atomic here).
+// hid (optional): both entries of a pair get the half-edge id i * kSlotCap + q.
 __global__ void k_fill(int64_t N, const uint32_t* __restrict__ hslot,
                        const uint32_t* __restrict__ hcnt, const uint32_t* __restrict__ indeg,
                        const uint32_t* __restrict__ row_ptr, uint32_t* __restrict__ lcur,
-                       uint32_t* __restrict__ col, uint32_t* __restrict__ hid,
-                       const uint32_t* __restrict__ rank) {
+                       uint32_t* __restrict__ col, uint32_t* __restrict__ hid) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint32_t n = min(hcnt[i], (uint32_t)kSlotCap);
@@ -127,7 +121,7 @@ __global__ void k_fill(int64_t N, const uint32_t* __restrict__ hslot,
   for (uint32_t q = 0; q < n; ++q) {
     const uint32_t jv = hslot[i * (int64_t)kSlotCap + q];
     const uint32_t j = jv & kIndexMask;
-    const uint32_t lo = row_ptr[j] + (rank ? rank[i * (int64_t)kSlotCap + q] : atomicAdd(&lcur[j], 1u));
+    const uint32_t lo = row_ptr[j] + atomicAdd(&lcur[j], 1u);
     col[up + q] = jv;
     col[lo] = (uint32_t)i | (jv & kExchOnly);
     if (hid) {
@@ -143,14 +137,13 @@ __global__ void k_fill_ovf(unsigned long long n, uint32_t N, const uint32_t* __r
                            const uint32_t* __restrict__ indeg,
                            const uint32_t* __restrict__ row_ptr, uint32_t* __restrict__ lcur,
                            uint32_t* __restrict__ ocur, uint32_t* __restrict__ col,
-                           uint32_t* __restrict__ hid, const uint32_t* __restrict__ rank) {
+                           uint32_t* __restrict__ hid) {
   const unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
   if (q >= n) return;
   const uint32_t i = ovf[2 * q], jv = ovf[2 * q + 1];
   const uint32_t j = jv & kIndexMask;
   const uint32_t up = row_ptr[i] + indeg[i] + kSlotCap + atomicAdd(&ocur[i], 1u);
-  const uint32_t lo =
-      row_ptr[j] + (rank ? rank[(size_t)N * kSlotCap + q] : atomicAdd(&lcur[j], 1u));
+  const uint32_t lo = row_ptr[j] + atomicAdd(&lcur[j], 1u);
   col[up] = jv;
   col[lo] = i | (jv & kExchOnly);
   if (hid) {
@@ -212,10 +205,10 @@ cudaError_t csr_scan(const DevParams& P, SwitchBufs& b, uint32_t* row_ptr, DevCo
 cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* row_ptr,
                      uint32_t* col, uint32_t* hid, bool has_overflow, bool sort_rows,
                      DevCounters* cnt, cudaStream_t st, int64_t* launches) {
-  cudaError_t e = b.rank ? cudaSuccess : cudaMemsetAsync(b.lcur, 0, P.N * sizeof(uint32_t), st);
+  cudaError_t e = cudaMemsetAsync(b.lcur, 0, P.N * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((P.N + 255) / 256);
-  k_fill<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, b.indeg, row_ptr, b.lcur, col, hid, b.rank);
+  k_fill<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, b.indeg, row_ptr, b.lcur, col, hid);
   ++*launches;
   if (has_overflow) {
     unsigned long long n = 0;
@@ -227,8 +220,7 @@ cudaError_t csr_fill(const DevParams& P, const SwitchBufs& b, const uint32_t* ro
     if (e != cudaSuccess) return e;
     if (n > 0) {
       k_fill_ovf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, (uint32_t)P.N, b.ovf, b.indeg,
-                                                              row_ptr, b.lcur, b.ocur, col, hid,
-                                                              b.rank);
+                                                              row_ptr, b.lcur, b.ocur, col, hid);
       ++*launches;
     }
   }

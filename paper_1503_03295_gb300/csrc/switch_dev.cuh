@@ -191,14 +191,16 @@ __device__ __noinline__ bool survives_dd(const DevParams& P, double si0, double 
 // 1 - P_ij = -expm1(beta (V - Vmax)) of the pair (S_i at i, S_j at i + (dx, dy)) in FP64 from the
 // beta-scaled pair table t: x = a1 (S_i.S_j) - (S_i.a3 d)(S_j.d) - bvm, |x error| <= c0 +
 // 2^-52 |x| (c0 covers the roundings), then expm1_np (relative error kExpm1RelErr).
+// x itself is returned in *x.
 __device__ __forceinline__ double pair_keep64(const Sw64& t, const double* Si, const double* Sj,
-                                              int32_t dx, int32_t dy) {
+                                              int32_t dx, int32_t dy, double* x) {
   const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
   const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
   const double ss = Si[0] * Sj[0] + Si[1] * Sj[1] + Si[2] * Sj[2];
   const double pa = Si[0] * ax3 + Si[1] * ay3;
   const double pb = Sj[0] * fx + Sj[1] * fy;
   const double b = fma(t.a1, ss, fma(-pa, pb, -t.bvm));  // c0 covers these two roundings
+  *x = b;
   return -expm1_np(b);
 }
 
@@ -209,8 +211,8 @@ __device__ __forceinline__ double pair_keep64(const Sw64& t, const double* Si, c
 __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t, double q,
                                               const double* Si, const double* Sj, int32_t dx,
                                               int32_t dy, uint64_t A, double u1,
-                                              unsigned& ghits, double& keep) {
-  const double pr = pair_keep64(t, Si, Sj, dx, dy);
+                                              unsigned& ghits, double& keep, double& xk) {
+  const double pr = pair_keep64(t, Si, Sj, dx, dy, &xk);
   keep = pr;
   const double mu = pr - u1 * q;
   // mu > bsw, mu < -bsw on ordered bit images (bsw > 0: ord(-bsw) = -ord(bsw) - 1)
@@ -254,15 +256,16 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
   const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * (dy < 0 ? -dy : dy);
   const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
   const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-  double keep;
-  return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, A, u53(wU), ghits, keep);
+  double keep, xk;
+  return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, A, u53(wU), ghits, keep, xk);
 }
 
 // Where a site writes its upper neighbours: kSlotCap slots of its own (row `id` of hslot), then
 // an overflow list shared by all sites (entry: site id, j | flag).  indeg counts lower
-// neighbours per (local) site.  keep / keep_ovf (optional, FP64 form): the FP64 value of
-// 1 - P_ij of each surviving dipolar pair, written to the x field of the pair-cache record at
-// the same slot or overflow index (the cache that the FP64 sweep starts from).
+// neighbours per (local) site.  keep / keep_ovf (optional, FP64 form): the FP64 values of
+// 1 - P_ij and of x = beta (V - Vmax) of each surviving dipolar pair, written to the first half
+// of the pair-cache record at the same slot or overflow index (the cache that the FP64 sweep
+// starts from).
 struct SwitchOut {
   uint32_t* hslot;
   uint32_t* indeg;
@@ -272,11 +275,6 @@ struct SwitchOut {
   int* status;
   double4_32a* keep = nullptr;
   double4_32a* keep_ovf = nullptr;
-  // rank / rank_ovf (optional): the half-edge's ticket among the lower neighbours of j (the
-  // value its atomic on indeg[j] returned), which places the pair in j's row without a second
-  // atomic
-  uint32_t* rank = nullptr;
-  uint32_t* rank_ovf = nullptr;
 };
 
 // One site's walk along its half-plane list: the candidate search of Sec. 2.1 with the state it
@@ -298,24 +296,23 @@ struct SiteWalk {
 };
 
 __device__ __forceinline__ void switch_emit(const SwitchOut& o, uint32_t id, uint32_t& n_out,
-                                            uint32_t jv, double keep = 0.0) {
-  const uint32_t rk = atomicAdd(&o.indeg[jv & kIndexMask], 1u);
+                                            uint32_t jv, double keep = 0.0, double xk = 0.0) {
   if (n_out < (uint32_t)kSlotCap) {
     o.hslot[(size_t)id * kSlotCap + n_out] = jv;
-    if (o.keep) o.keep[(size_t)id * kSlotCap + n_out].x = keep;
-    if (o.rank) o.rank[(size_t)id * kSlotCap + n_out] = rk;
+    if (o.keep)
+      *reinterpret_cast<double2*>(&o.keep[(size_t)id * kSlotCap + n_out]) = make_double2(keep, xk);
   } else {
     const unsigned long long idx = atomicAdd(o.ovf_n, 1ull);
     if (idx < o.ovf_cap) {
       o.ovf[2 * idx] = id;
       o.ovf[2 * idx + 1] = jv;
-      if (o.keep) o.keep_ovf[idx].x = keep;
-      if (o.rank) o.rank_ovf[idx] = rk;
+      if (o.keep) *reinterpret_cast<double2*>(&o.keep_ovf[idx]) = make_double2(keep, xk);
     } else {
       set_status(o.status, kStatusCapacity);
     }
   }
   ++n_out;
+  atomicAdd(&o.indeg[jv & kIndexMask], 1u);
 }
 
 template <int PREC>
@@ -373,7 +370,7 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
     const uint64_t A = Wk - (k > 0 ? T.w(k - 1) : 0ull);
     const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
     bool surv;
-    double keep = 0.0;
+    double keep = 0.0, xk = 0.0;
     if (PREC == 1) {
       const float4 sj = s32[j];
       const float Sj32[3] = {sj.x, sj.y, sj.z};
@@ -382,10 +379,10 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
     } else {
       const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
       surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), a.Si, Sj, dx, dy, A, u53(wU), ghits,
-                           keep);
+                           keep, xk);
     }
     if (surv) {
-      switch_emit(o, a.id, a.n_out, (uint32_t)j, keep);
+      switch_emit(o, a.id, a.n_out, (uint32_t)j, keep, xk);
       ++n_dip;
       if (k == mnn0) a.nn0 = true;
       if (k == mnn1) a.nn1 = true;
