@@ -179,8 +179,8 @@ FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal: context
 # FP64 sweep kernels, per pair of the switched graph and per spin update, from one ncu capture
 # of the current kernels on a smaller lattice at T = 0.6 D (DRAM bytes and executed FP64
 # thread-instructions scale with the updates and pairs, not with L): see the named profile
-SWEEP64_EXECUTED_FP64_PER_PAIR = 42.9  # k_propose + k_sweep + k_resolve, thread-instructions
-SWEEP64_DRAM_BYTES_PER_UPDATE = 2656.0  # dram__bytes_read.sum + dram__bytes_write.sum
+SWEEP64_EXECUTED_FP64_PER_PAIR = 39.5  # k_propose + k_sweep + k_resolve, thread-instructions
+SWEEP64_DRAM_BYTES_PER_UPDATE = 2652.0  # dram__bytes_read.sum + dram__bytes_write.sum
 SWEEP64_TRAFFIC_T = 0.6
 SWEEP64_EXECUTED_SOURCE = "profiles/k_sweep_fp64_L1024_T0.6.md"
 
@@ -206,12 +206,17 @@ def low_levels(g, M):
     return p
 
 
-def algorithmic_bytes(k, M, p0):
+def algorithmic_bytes(k, M, p0, cache=False):
     """Bytes per spin update that each phase must move at least once, k the mean degree, M the
     KW levels and p0 the block-local ones: switch + CSR 40 + 16k; colouring + classes: the
     first p0 levels read the rows once and write the colours (4 + 4k + 9), every later level
-    half the rows and colours (4 + 2k), classes 12; sweep 60 + 8k."""
+    half the rows and colours (4 + 2k), classes 12; sweep 60 + 8k.  With the FP64 form's pair
+    cache (cache=True) the switch also writes a 16-byte record per kept pair and the fill a
+    4-byte id per CSR entry (+12k), and the sweep reads per pair endpoint the id and one
+    16-byte record half and writes 16 bytes for one of the two endpoints (+28k)."""
     colour = (4 + 4 * k + 9 if p0 else 0) + (M - p0) * (4 + 2 * k) + 12
+    if cache:
+        return {"switch": 40 + 28 * k, "colour": colour, "sweep": 60 + 36 * k}
     return {"switch": 40 + 16 * k, "colour": colour, "sweep": 60 + 8 * k}
 
 
@@ -221,8 +226,8 @@ def algorithmic_flops(k, cand):
     two pair energies (20) and the pseudointeraction term of the proposed spin (50, a log1mexp
     counted as two transcendentals): the old spin's term is read from the pair cache, which the
     switch filled, so 70 (120 without the cache); the colouring has none.  The kernels issue
-    fewer (about 40 per candidate, 43 per pair endpoint: see SWEEP64_EXECUTED_FP64_PER_PAIR), so
-    these fractions measure work done against the plan."""
+    fewer (about 40 per candidate, 39.5 per pair endpoint: see SWEEP64_EXECUTED_FP64_PER_PAIR),
+    so these fractions measure work done against the plan."""
     return {"switch": 70.0 * cand, "colour": 0.0, "sweep": 70.0 * k}
 
 
@@ -234,8 +239,9 @@ def phase_ms(ph):
 
 def rooflines(per_step, N, k, M, p0, cand, hbm, how, fp64_gflops=None):
     """HBM roofline of every phase and, for the FP64 form (fp64_gflops: the measured FP64
-    peak), the FP64-ALU roofline against the planning operation counts."""
-    ab = algorithmic_bytes(k, M, p0)
+    peak; its bytes include the pair cache), the FP64-ALU roofline against the planning
+    operation counts."""
+    ab = algorithmic_bytes(k, M, p0, cache=bool(fp64_gflops))
     af = algorithmic_flops(k, cand)
     out = {}
     for ph, ms in per_step.items():

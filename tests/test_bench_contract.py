@@ -50,6 +50,11 @@ def test_algorithmic_work_figures():
     assert abs(b["switch"] - (40 + 16 * k)) < 1e-9
     assert abs(b["colour"] - ((4 + 4 * k + 9) + (M - p0) * (4 + 2 * k) + 12)) < 1e-9
     assert abs(b["sweep"] - (60 + 8 * k)) < 1e-9
+    # the FP64 form's pair cache: 16-byte records and 4-byte ids written by switch and fill,
+    # read (and half written) by the sweep
+    c = bench.algorithmic_bytes(k, M, p0, cache=True)
+    assert abs(c["switch"] - (40 + 28 * k)) < 1e-9 and abs(c["sweep"] - (60 + 36 * k)) < 1e-9
+    assert c["colour"] == b["colour"]
     # no block-local level: every level reads half the rows
     assert abs(bench.algorithmic_bytes(k, M, 0)["colour"] - (M * (4 + 2 * k) + 12)) < 1e-9
     f = bench.algorithmic_flops(k, 14.4)
