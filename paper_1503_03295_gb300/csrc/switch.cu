@@ -118,16 +118,29 @@ __global__ void k_fill(int64_t N, const uint32_t* __restrict__ hslot,
   if (i >= N) return;
   const uint32_t n = min(hcnt[i], (uint32_t)kSlotCap);
   const uint32_t up = row_ptr[i] + indeg[i];
-  for (uint32_t q = 0; q < n; ++q) {
-    const uint32_t jv = hslot[i * (int64_t)kSlotCap + q];
-    const uint32_t j = jv & kIndexMask;
-    const uint32_t lo = row_ptr[j] + atomicAdd(&lcur[j], 1u);
-    col[up + q] = jv;
-    col[lo] = (uint32_t)i | (jv & kExchOnly);
-    if (hid) {
-      const uint32_t h = (uint32_t)i * (uint32_t)kSlotCap + q;
-      hid[up + q] = h;
-      hid[lo] = h;
+  // eight half-edges at a time: their slot and row-pointer loads, then their atomics, then their
+  // stores, each group issued together (the atomics' returns were the chain)
+  constexpr uint32_t kB = 8;
+  for (uint32_t q0 = 0; q0 < n; q0 += kB) {
+    uint32_t jv[kB], base[kB], lo[kB];
+#pragma unroll
+    for (uint32_t a = 0; a < kB; ++a)
+      jv[a] = q0 + a < n ? hslot[i * (int64_t)kSlotCap + q0 + a] : 0u;
+#pragma unroll
+    for (uint32_t a = 0; a < kB; ++a) base[a] = q0 + a < n ? row_ptr[jv[a] & kIndexMask] : 0u;
+#pragma unroll
+    for (uint32_t a = 0; a < kB; ++a)
+      lo[a] = q0 + a < n ? base[a] + atomicAdd(&lcur[jv[a] & kIndexMask], 1u) : 0u;
+#pragma unroll
+    for (uint32_t a = 0; a < kB; ++a) {
+      if (q0 + a >= n) continue;
+      col[up + q0 + a] = jv[a];
+      col[lo[a]] = (uint32_t)i | (jv[a] & kExchOnly);
+      if (hid) {
+        const uint32_t h = (uint32_t)i * (uint32_t)kSlotCap + q0 + a;
+        hid[up + q0 + a] = h;
+        hid[lo[a]] = h;
+      }
     }
   }
 }
