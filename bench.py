@@ -64,6 +64,9 @@ def parse():
                     help="MC steps per run of the L=1024 FP32-guarded vs FP64 comparison at "
                          "T = 0.4 D and 0.8 D; 0 skips it")
     ap.add_argument("--prec-L", type=int, default=1024)
+    ap.add_argument("--nsw100-steps", type=int, default=100,
+                    help="MC steps of the FP64 run with switch + colour every 100 steps (the "
+                         "paper's n_sw, Eq. (8)'s t_ave); 0 skips it")
     ap.add_argument("--no-kw-bound", action="store_true",
                     help="skip t_R of both colour-reduction variants against Eq. (5)'s bound")
     ap.add_argument("--protocol", action="store_true",
@@ -338,6 +341,8 @@ def run_ours(args, rank, world, local):
         del lat32
     if args.long_steps > 0:
         out["long"] = run_long(args, rank, world, dev, stream)
+    if args.nsw100_steps > 0:
+        out["n_sw_100"] = run_nsw100(args, rank, world, dev, stream)
     if args.prec_steps > 0:
         out["precision"] = run_precision(args, rank, world, dev, stream)
     if not args.no_kw_bound:
@@ -408,6 +413,36 @@ def run_long(args, rank, world, dev, stream):
             "e_switched_per_spin_end": o["e_switched"] / N,
             "workload": "L=%d, J=0, D=1, T=%gD, seed %d, n_sw=1, FP64, %d MC steps from the "
                         "random start" % (args.L, args.T, args.seed, K)}
+
+
+def run_nsw100(args, rank, world, dev, stream):
+    """The paper's schedule on the benchmark lattice: switch and colour every n_sw = 100 MC
+    steps (Sec. 3.1), FP64.  Eq. (8)'s t_ave = t_switch / 100 + t_color / 100 + t_MC, from the
+    phase times of K steps (K / 100 switches); the graph of each epoch carries the pair cache
+    from one step to the next."""
+    import paper_1503_03295_gb300 as sco
+
+    K = args.nsw100_steps
+    lat = sco.Lattice(sco.make_params(args.L, T=args.T, seed=rank_seed(args.seed, rank),
+                                      n_sw=100), stream=stream.cuda_stream)
+    lat.sweep(100)  # one whole epoch untimed (warm-up)
+    lat.sync()
+    lat.set_timing(True)
+    ms = max_over_ranks(_timed_steps(lat, K, dev, stream), world, dev)
+    ph = lat.timing()
+    lat.set_timing(False)
+    lat.close()
+    N = args.L * args.L
+    t_sw = ph["switch_ms"] / max(ph["switch_calls"], 1)
+    t_col = ph["colour_ms"] / max(ph["colour_calls"], 1)
+    t_mc = ph["sweep_ms"] / max(ph["sweep_calls"], 1)
+    return {"steps": K, "n_sw": 100, "precision": "fp64",
+            "value": whole_job_rate(N, K, world, ms), "ms_per_step": ms / K,
+            "t_switch_ms": t_sw, "t_color_ms": t_col, "t_mc_ms": t_mc,
+            "t_ave_ms": t_sw / 100 + t_col / 100 + t_mc,
+            "switches": ph["switch_calls"],
+            "workload": "L=%d, J=0, D=1, T=%gD, seed %d, n_sw=100, FP64, %d MC steps after one "
+                        "epoch" % (args.L, args.T, args.seed, K)}
 
 
 def run_precision(args, rank, world, dev, stream):
@@ -767,7 +802,7 @@ def main():
     line["fp64_peak"] = {"gflops": fpk["gflops"], "dfma_per_s": fpk["dfma_per_s"],
                          "expm1_per_s": fpk["expm1_per_s"], "log_per_s": fpk["log_per_s"],
                          "clocks": fpk["clocks"], "nominal_gflops": FP64_NOMINAL_GFLOPS}
-    for key in ("long", "precision", "kw_bound", "graph_stats"):
+    for key in ("long", "n_sw_100", "precision", "kw_bound", "graph_stats"):
         if key in res:
             line[key] = res[key]
     if "batch" in res:

@@ -186,7 +186,7 @@ def test_checkpoint_resume_bit_exact():
 @pytest.mark.slow
 def test_full_size_first_sweep_L2304():
     """The workload size of the throughput benchmark: L = 2304, T = 0.6 D, seed 0, in both
-    forms the benchmark times (FP64 and FP32-guarded), against one oracle MC step."""
+    forms the benchmark times (FP64 and FP32-guarded), against two oracle MC steps."""
     g, o = _pair(2304, T=0.6, seed=0)
     t = g.table()
     r = O.table(2304)
@@ -209,9 +209,14 @@ def test_full_size_first_sweep_L2304():
         assert np.array_equal(a["pairs"], b["pairs"])
         assert a["delta_r_weighted"] == b["delta_r_weighted"]
         assert np.array_equal(a["delta_r"], b["delta_r"], equal_nan=True)
+    # a second MC step (a new switch, the FP64 pair cache filled again)
+    g.sweep(1)
+    o.sweep(1)
+    assert np.array_equal(g.accepts(), o.accepts())
+    assert np.array_equal(g.spins(), o.spins())
     g.close()
     g32 = sco.Lattice(sco.make_params(2304, T=0.6, seed=0, precision=sco.FP32_GUARDED))
-    g32.sweep(1)
+    g32.sweep(2)
     _same_graph(g32, o)
     assert np.array_equal(g32.colours().astype(np.int32), o.colours())
     assert np.array_equal(g32.spins(), o.spins())
