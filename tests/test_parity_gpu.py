@@ -214,6 +214,9 @@ def test_full_size_first_sweep_L2304():
     o.sweep(1)
     assert np.array_equal(g.accepts(), o.accepts())
     assert np.array_equal(g.spins(), o.spins())
+    og, oo = g.observables(), o.observables()
+    assert og["kw_rounds"] == oo["kw_rounds"]
+    _same_energy(og["e_switched"], oo["e_switched"], g.N)
     g.close()
     g32 = sco.Lattice(sco.make_params(2304, T=0.6, seed=0, precision=sco.FP32_GUARDED))
     g32.sweep(2)
