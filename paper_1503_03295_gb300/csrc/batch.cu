@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256, 4) kb_switch(const BatchDev B) {
     sD[q] = disp[q];
   }
   __syncthreads();
-  const NearTable T{sW, sD, W, disp, nnear, K};
+  const NearTable T{sW, sD, W, disp, nnear, K, nnear};
   const uint32_t base = d->base;
   const uint32_t i = (blockIdx.x - B.blk_start[r]) * kBatchBlock + threadIdx.x;
   unsigned long long n_half = 0, n_dip = 0;

@@ -44,6 +44,10 @@ struct Table {
   int64_t K = 0;
   uint32_t* disp = nullptr;  // packed (dx & 0xFFFF) | (dy << 16), sorted by (r^2, dy, dx)
   uint64_t* W = nullptr;     // inclusive prefix of the integer hazards A_m
+  // by list index m: the bits of fl(exp(-beta D 2^-58 W_m)), the probability that a walk from
+  // the list's start passes m without a candidate (FP64 candidate search; temperature-dependent,
+  // built with the tables by (|dx|, |dy|) once the list exists)
+  uint64_t* Ebits = nullptr;
   double2* xy = nullptr;     // by (|dx|, |dy|): {fl(D c(r^2)), V_max = fl(fl(D A) 2^-59)}
   double* xyq = nullptr;     // by (|dx|, |dy|): q = -expm1(-2 beta V_max), candidate probability
   float4* xy32 = nullptr;    // by (|dx|, |dy|): FP32 copies {Dc, Vmax, 2 beta Vmax, q}

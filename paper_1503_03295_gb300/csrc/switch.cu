@@ -16,6 +16,7 @@ namespace {
 // takes the same time there with half the register spills.
 template <int PREC>
 __global__ void __launch_bounds__(256, PREC == 1 ? 5 : 4) k_switch(const DevParams P, const uint64_t* __restrict__ W,
+                                                const uint64_t* __restrict__ Eb,
                                                 const uint32_t* __restrict__ disp,
                                                 const Sw64* __restrict__ sw64,
                                                 const double* __restrict__ xyq,
@@ -24,15 +25,22 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 5 : 4) k_switch(const DevPara
                                                 const float4* __restrict__ s32, uint32_t epoch,
                                                 int32_t mnn0, int32_t mnn1, SwitchBufs b,
                                                 DevCounters* __restrict__ cnt) {
-  __shared__ uint64_t sW[kNear];
+  // the head of the list: W (FP32-screened search) or the decay bits (FP64 search)
+  __shared__ uint64_t sX[kNear];
   __shared__ uint32_t sD[kNear];
+  const bool decay = PREC == 0 && Eb != nullptr;
   const int64_t nnear = P.K < kNear ? P.K : kNear;
   for (int q = threadIdx.x; q < nnear; q += blockDim.x) {
-    sW[q] = W[q];
+    sX[q] = decay ? Eb[q] : W[q];
     sD[q] = disp[q];
   }
   __syncthreads();
-  const NearTable T{sW, sD, W, disp, nnear, P.K};
+  NearTable T{sX, sD, W, disp, nnear, P.K, nnear};
+  if (decay) {
+    T.nw = 0;
+    T.sE = sX;
+    T.E = Eb;
+  }
   const uint64_t Wtot = P.K > 0 ? __ldg(&W[P.K - 1]) : 0;
   SwitchOut o{b.hslot, b.indeg, b.ovf, b.ovf_cap, &cnt->ovf_n, &cnt->ovf_full};
   if (PREC == 0 && b.keep) {
@@ -64,7 +72,7 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 5 : 4) k_switch(const DevPara
       const uint32_t take = min((uint32_t)__popc(need), pool_n);
       const uint32_t rank = (uint32_t)__popc(need & below);
       if (!active && rank < take) {
-        walk_begin<PREC>(P, s, s32, pool + rank, pool + rank, a);
+        walk_begin<PREC>(P, T, s, s32, pool + rank, pool + rank, a);
         active = true;
       }
       pool += take;
@@ -198,11 +206,11 @@ cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, cons
   if (nb64 > (P.N + 255) / 256) nb64 = (P.N + 255) / 256;
   const unsigned nb = (unsigned)nb64;
   if (precision == 1)
-    k_switch<1><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.sw64, t.xyq, t.xy32, s, s32, epoch,
-                                     t.m_nn[0], t.m_nn[1], b, cnt);
+    k_switch<1><<<nb, 256, 0, st>>>(P, t.W, nullptr, t.disp, t.sw64, t.xyq, t.xy32, s, s32,
+                                     epoch, t.m_nn[0], t.m_nn[1], b, cnt);
   else
-    k_switch<0><<<nb, 256, 0, st>>>(P, t.W, t.disp, t.sw64, t.xyq, t.xy32, s, s32, epoch,
-                                     t.m_nn[0], t.m_nn[1], b, cnt);
+    k_switch<0><<<nb, 256, 0, st>>>(P, t.W, t.Ebits, t.disp, t.sw64, t.xyq, t.xy32, s, s32,
+                                     epoch, t.m_nn[0], t.m_nn[1], b, cnt);
   ++*launches;
   return cudaGetLastError();
 }

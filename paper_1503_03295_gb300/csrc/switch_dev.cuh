@@ -25,24 +25,52 @@ constexpr int kStatusCapacity = 7;
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
+// The sorted half-plane list as a walk reads it: displacements d, the hazard prefix W and (FP64
+// search) the decay bits E of Table::Ebits, the first nnear displacements in shared memory with
+// the first nw entries of W (nw = nnear, or 0 when the shared array holds E instead).
 struct NearTable {
   const uint64_t* sW;
   const uint32_t* sD;
   const uint64_t* W;
   const uint32_t* disp;
-  int64_t nnear, K;
-  __device__ __forceinline__ uint64_t w(int64_t k) const { return k < nnear ? sW[k] : __ldg(&W[k]); }
+  int64_t nnear, K, nw;
+  const uint64_t* sE = nullptr;  // first nnear decay bits (FP64 search), or nullptr
+  const uint64_t* E = nullptr;   // all K decay bits, or nullptr: search W with a logarithm
+  __device__ __forceinline__ uint64_t w(int64_t k) const { return k < nw ? sW[k] : __ldg(&W[k]); }
   __device__ __forceinline__ uint32_t d(int64_t k) const {
     return k < nnear ? sD[k] : __ldg(&disp[k]);
   }
+  __device__ __forceinline__ uint64_t e(int64_t k) const {
+    return k < nnear ? sE[k] : __ldg(&E[k]);
+  }
   // first k in [lo, K) with W[k] >= target, K if none
   __device__ __forceinline__ int64_t lower_bound(int64_t lo, uint64_t target) const {
-    if (lo < nnear) {
-      if (sW[nnear - 1] >= target) {
-        int64_t a = lo, b = nnear - 1;
+    if (lo < nw) {
+      if (sW[nw - 1] >= target) {
+        int64_t a = lo, b = nw - 1;
         while (a < b) {
           const int64_t mid = (a + b) >> 1;
           if (sW[mid] >= target) b = mid; else a = mid + 1;
+        }
+        return a;
+      }
+      lo = nw;
+    }
+    int64_t a = lo, b = K;
+    while (a < b) {
+      const int64_t mid = (a + b) >> 1;
+      if (__ldg(&W[mid]) >= target) b = mid; else a = mid + 1;
+    }
+    return a;
+  }
+  // first k in [lo, K) with E[k] <= target (E is non-increasing), K if none
+  __device__ __forceinline__ int64_t lower_bound_e(int64_t lo, uint64_t target) const {
+    if (lo < nnear) {
+      if (sE[nnear - 1] <= target) {
+        int64_t a = lo, b = nnear - 1;
+        while (a < b) {
+          const int64_t mid = (a + b) >> 1;
+          if (sE[mid] <= target) b = mid; else a = mid + 1;
         }
         return a;
       }
@@ -51,7 +79,7 @@ struct NearTable {
     int64_t a = lo, b = K;
     while (a < b) {
       const int64_t mid = (a + b) >> 1;
-      if (__ldg(&W[mid]) >= target) b = mid; else a = mid + 1;
+      if (__ldg(&E[mid]) <= target) b = mid; else a = mid + 1;
     }
     return a;
   }
@@ -126,6 +154,40 @@ __device__ __forceinline__ int64_t next_candidate(const DevParams& P, const Near
   if (certain) return k;
   ++ghits;
   return next_candidate_dd(P, T, s, Ws, up);
+}
+
+// Bits of 1.0: the decay value before the first element (W = 0).
+constexpr uint64_t kDecayStart = 0x3FF0000000000000ull;
+// Targets below 2^-990 take the exact search (the decay table's values there are not normal).
+constexpr uint64_t kDecayMinBits = 0x0210000000000000ull;
+
+// FP64 candidate search without a logarithm.  With E*_m = exp(-beta D 2^-58 W_m) the next
+// candidate min { k > s : beta D 2^-58 (W_k - W_s) >= -ln u+ } is min { k > s : E*_k <= u+ E*_s }
+// (exp is increasing), searched on the table's bits: E_m within 2^-52 of E*_m, the target
+// fl(u+ E_s) within 2^-51.9 of u+ E*_s.  Positive doubles order as their bit images, and 16
+// units in the last place are at least 2^-49 relative, more than the combined error, so the
+// candidate is certain when E_k's bits lie at least 16 below the target's and E_(k-1)'s at least
+// 16 above; otherwise (or for a target below 2^-990) the search with the logarithm decides.
+// Es carries the bits of E at the walk's last candidate and is advanced to the new one.
+__device__ __forceinline__ int64_t next_candidate_e(const DevParams& P, const NearTable& T,
+                                                    int64_t s, uint64_t& Es, uint64_t Wtot,
+                                                    uint64_t wE, unsigned& ghits) {
+  if (s >= T.K - 1 || !P.switching) return T.K;
+  const uint64_t tb = (uint64_t)__double_as_longlong(u53pos(wE) * __longlong_as_double(Es));
+  if (tb >= kDecayMinBits) {
+    const int64_t k = T.lower_bound_e(s + 1, tb);
+    const uint64_t ek = k < T.K ? T.e(k) : 0ull;
+    bool certain = true;
+    if (k < T.K && ek + 16ull > tb) certain = false;
+    if (k - 1 > s && T.e(k - 1) < tb + 16ull) certain = false;
+    if (certain) {
+      Es = ek;
+      return k;
+    }
+  }
+  const int64_t k = next_candidate(P, T, s, s >= 0 ? T.w(s) : 0ull, Wtot, wE, ghits);
+  if (k < T.K) Es = T.e(k);
+  return k;
 }
 
 // FP32 screen of the candidate search.  E = -ln u+ is taken as -log1pf(-(1 - u+)) above 1/2
@@ -204,14 +266,20 @@ __device__ __forceinline__ double pair_keep64(const Sw64& t, const double* Si, c
   return -expm1_np(b);
 }
 
+// The integer hazard A_k of list element k (only the double-double tests need it).
+__device__ __forceinline__ uint64_t hazard_of(const NearTable& T, int64_t k) {
+  return T.w(k) - (k > 0 ? T.w(k - 1) : 0ull);
+}
+
 // FP64 survival test u q < 1 - P_ij: x = beta (V - Vmax) from the beta-scaled pair table
 // (t, the sweep's Sw64 entry), 1 - P = -expm1_np(x), margin bound t.bsw (precomputed: |dx| <=
 // c0, expm1_np within kExpm1RelErr, q within 2^-50, two roundings; doubled).  u is exact.
 // `keep` receives the FP64 value of 1 - P (within its error bound whatever the decision).
 __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t, double q,
                                               const double* Si, const double* Sj, int32_t dx,
-                                              int32_t dy, uint64_t A, double u1,
-                                              unsigned& ghits, double& keep, double& xk) {
+                                              int32_t dy, const NearTable& T, int64_t k,
+                                              double u1, unsigned& ghits, double& keep,
+                                              double& xk) {
   const double pr = pair_keep64(t, Si, Sj, dx, dy, &xk);
   keep = pr;
   const double mu = pr - u1 * q;
@@ -220,7 +288,7 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t,
   if (om > ob) return true;
   if (om < -ob - 1) return false;
   ++ghits;
-  return survives_dd(P, Si[0], Si[1], Si[2], Sj[0], Sj[1], Sj[2], dx, dy, A, u1);
+  return survives_dd(P, Si[0], Si[1], Si[2], Sj[0], Sj[1], Sj[2], dx, dy, hazard_of(T, k), u1);
 }
 
 // FP32 screen of the same test (FP32-guarded form): spins from the FP32 shadow
@@ -231,8 +299,9 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
                                               const Sw64* __restrict__ sw, double q64,
                                               const float* Si32, const float* Sj32,
                                               const double* __restrict__ s, int64_t i, int64_t j,
-                                              int32_t dx, int32_t dy, uint64_t A, uint64_t wU,
-                                              unsigned& g32, unsigned& ghits) {
+                                              int32_t dx, int32_t dy, const NearTable& T,
+                                              int64_t k, uint64_t wU, unsigned& g32,
+                                              unsigned& ghits) {
   const float fr2 = (float)(dx * dx + dy * dy), fx = (float)dx, fy = (float)dy;
   // u truncated to 24 bits: 0 <= u - u24 < 2^-24, inside the 2^-19 q term of the bound
   const float u24 = __uint2float_rn((uint32_t)(wU >> 40)) * 0x1p-24f;
@@ -257,7 +326,7 @@ __device__ __forceinline__ bool survives_fp32(const DevParams& P, float4 t32,
   const double Si[3] = {s[i], s[P.N + i], s[2 * P.N + i]};
   const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
   double keep, xk;
-  return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, A, u53(wU), ghits, keep, xk);
+  return survives_fp64(P, sw[tix], q64, Si, Sj, dx, dy, T, k, u53(wU), ghits, keep, xk);
 }
 
 // Where a site writes its upper neighbours: kSlotCap slots of its own (row `id` of hslot), then
@@ -288,7 +357,7 @@ struct SiteWalk {
   double Si[3];    // FP64 form
   float Si32[3];   // FP32-screened form
   int64_t sidx;    // last candidate (-1 before the first)
-  uint64_t Ws;     // W at sidx
+  uint64_t Ws;     // W at sidx, or with the decay table the bits of E at sidx
   uint32_t n;      // candidates drawn; Philox block n / 2, words 0-1 or 2-3
   W4 w;
   uint32_t n_out;
@@ -316,7 +385,8 @@ __device__ __forceinline__ void switch_emit(const SwitchOut& o, uint32_t id, uin
 }
 
 template <int PREC>
-__device__ __forceinline__ void walk_begin(const DevParams& P, const double* __restrict__ s,
+__device__ __forceinline__ void walk_begin(const DevParams& P, const NearTable& T,
+                                           const double* __restrict__ s,
                                            const float4* __restrict__ s32, uint32_t i,
                                            uint32_t id, SiteWalk<PREC>& a) {
   a.i = i;
@@ -334,7 +404,7 @@ __device__ __forceinline__ void walk_begin(const DevParams& P, const double* __r
     a.Si32[2] = si.z;
   }
   a.sidx = -1;
-  a.Ws = 0;
+  a.Ws = PREC == 0 && T.E ? kDecayStart : 0ull;
   a.n = 0;
   a.n_out = 0;
   a.nn0 = false;
@@ -358,16 +428,16 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
   const uint64_t wE = (a.n & 1u) ? a.w.w[2] : a.w.w[0];
   const uint64_t wU = (a.n & 1u) ? a.w.w[3] : a.w.w[1];
   ++a.n;
+  const bool decay = PREC == 0 && T.E != nullptr;  // uniform
   const int64_t k = PREC == 1 ? next_candidate_fp32(P, T, a.sidx, a.Ws, Wtot, wE, g32, ghits)
+                    : decay   ? next_candidate_e(P, T, a.sidx, a.Ws, Wtot, wE, ghits)
                               : next_candidate(P, T, a.sidx, a.Ws, Wtot, wE, ghits);
   if (k >= P.K) return false;
   const uint32_t d = T.d(k);
   const int32_t dx = (int16_t)(d & 0xFFFFu), dy = (int32_t)(d >> 16);
-  const uint64_t Wk = T.w(k);
   const int32_t xj = a.xi + dx, yj = a.yi + dy;
   if (xj >= 0 && xj < P.Lx && yj < P.Ly) {
     const int64_t j = xj + (int64_t)P.Lx * yj;
-    const uint64_t A = Wk - (k > 0 ? T.w(k - 1) : 0ull);
     const int64_t tix = (int64_t)(dx < 0 ? -dx : dx) + (int64_t)P.Lx * dy;
     bool surv;
     double keep = 0.0, xk = 0.0;
@@ -375,10 +445,10 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
       const float4 sj = s32[j];
       const float Sj32[3] = {sj.x, sj.y, sj.z};
       surv = survives_fp32(P, __ldg(&xy32[tix]), sw, __ldg(&xyq[tix]), a.Si32, Sj32, s,
-                           (int64_t)a.i, j, dx, dy, A, wU, g32, ghits);
+                           (int64_t)a.i, j, dx, dy, T, k, wU, g32, ghits);
     } else {
       const double Sj[3] = {s[j], s[P.N + j], s[2 * P.N + j]};
-      surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), a.Si, Sj, dx, dy, A, u53(wU), ghits,
+      surv = survives_fp64(P, sw[tix], __ldg(&xyq[tix]), a.Si, Sj, dx, dy, T, k, u53(wU), ghits,
                            keep, xk);
     }
     if (surv) {
@@ -389,7 +459,7 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
     }
   }
   a.sidx = k;
-  a.Ws = Wk;
+  if (!decay) a.Ws = T.w(k);
   return true;
 }
 
@@ -420,7 +490,7 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
                                                 unsigned long long& n_dip, unsigned& ghits,
                                                 unsigned& g32) {
   SiteWalk<PREC> a;
-  walk_begin<PREC>(P, s, s32, i, id, a);
+  walk_begin<PREC>(P, T, s, s32, i, id, a);
   while (walk_step<PREC>(P, T, Wtot, sw, xyq, xy32, s, s32, epoch, mnn0, mnn1, o, a, n_dip,
                          ghits, g32)) {
   }

@@ -111,6 +111,36 @@ __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __r
   sw32[q] = make_float4((float)a1, (float)a3, (float)bvm, (float)(c32 * (1.0 + 0x1p-20)));
 }
 
+// exp(x) of a double-double x <= 0 without the cancellation of 1 + expm1(x): x = k ln2 + r,
+// |r| <= ln2 / 2, e^x = 2^k (1 + expm1(r)); relative error of the double-double result far below
+// 2^-100 (the series and the reduction of dd_expm1_small / dd_expm1).
+__device__ dd exp_dd_neg(dd x, dd ln2) {
+  const double kf = floor(x.hi / ln2.hi + 0.5);
+  const dd r = dd_sub(x, dd_mul_d(ln2, kf));
+  return dd_ldexp(dd_add(dd_from(1.0), dd_expm1_small(r)), (int)kf);
+}
+
+// E_m = fl(exp(-beta D 2^-58 W_m)) as bits: the candidate process of the switch has rate
+// beta D A_m 2^-58 per element, so E_m is the probability of passing elements 0..m without a
+// candidate.  The exponent is formed exactly (beta D as a double-double product, W_m split into
+// two exact doubles), the exponential in double-double and rounded once, so E_m lies within
+// 2^-52 of its exact value (relative); below e^-690 (< 2^-995) it is stored as +0, which the
+// search treats as below every target it accepts (targets under 2^-990 take the exact path).
+__global__ void k_decay(int64_t K, double beta, double D, double ln2_hi, double ln2_lo,
+                        const uint64_t* __restrict__ W, uint64_t* __restrict__ Eb) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= K) return;
+  const uint64_t w = W[m];
+  const dd wd = dd_add(dd_from((double)(w >> 32) * 0x1p32), dd_from((double)(w & 0xFFFFFFFFull)));
+  const dd a = dd_ldexp(dd_mul(two_prod(beta, D), wd), -58);
+  double e = 0.0;
+  if (a.hi < 690.0) {
+    const dd x = exp_dd_neg(dd_neg(a), dd{ln2_hi, ln2_lo});
+    e = x.hi + x.lo;
+  }
+  Eb[m] = (uint64_t)__double_as_longlong(e);
+}
+
 }  // namespace
 
 cudaError_t table_build_xy(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches) {
@@ -124,6 +154,13 @@ cudaError_t table_build_xy(const DevParams& P, Table& t, cudaStream_t s, int64_t
   k_xy<<<(unsigned)((nxy + 255) / 256), 256, 0, s>>>(P.Lx, P.Ly, P.D, P.beta, t.xy, t.xyq,
                                                       t.xy32, t.sw64, t.sw32);
   ++*launches;
+  // the FP64 candidate search's decay values, where this table owns the sorted list
+  if (t.W && t.K > 0) {
+    if ((e = cudaMalloc(&t.Ebits, t.K * sizeof(uint64_t))) != cudaSuccess) return e;
+    k_decay<<<(unsigned)((t.K + 255) / 256), 256, 0, s>>>(t.K, P.beta, P.D, P.ln2_hi, P.ln2_lo,
+                                                          t.W, t.Ebits);
+    ++*launches;
+  }
   return cudaGetLastError();
 }
 
@@ -175,8 +212,8 @@ cudaError_t table_build_list(const DevParams& P, Table& t, cudaStream_t s, int64
 }
 
 cudaError_t table_build(const DevParams& P, Table& t, cudaStream_t s, int64_t* launches) {
-  cudaError_t e = table_build_xy(P, t, s, launches);
-  if (e == cudaSuccess) e = table_build_list(P, t, s, launches);
+  cudaError_t e = table_build_list(P, t, s, launches);
+  if (e == cudaSuccess) e = table_build_xy(P, t, s, launches);
   return e;
 }
 
@@ -186,6 +223,8 @@ void table_free_xy(Table& t) {
   cudaFree(t.xyq);
   cudaFree(t.sw64);
   cudaFree(t.sw32);
+  cudaFree(t.Ebits);
+  t.Ebits = nullptr;
   t.xy = nullptr;
   t.xy32 = nullptr;
   t.xyq = nullptr;
