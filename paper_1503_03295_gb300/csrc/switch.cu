@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 5 : 4) k_switch(const DevPara
     T.nw = 0;
     T.sE = sX;
     T.E = Eb;
+    T.elast = P.K > 0 ? __ldg(&Eb[P.K - 1]) : 0ull;
   }
   const uint64_t Wtot = P.K > 0 ? __ldg(&W[P.K - 1]) : 0;
   SwitchOut o{b.hslot, b.indeg, b.ovf, b.ovf_cap, &cnt->ovf_n, &cnt->ovf_full};

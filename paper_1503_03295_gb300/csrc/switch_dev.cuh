@@ -36,6 +36,7 @@ struct NearTable {
   int64_t nnear, K, nw;
   const uint64_t* sE = nullptr;  // first nnear decay bits (FP64 search), or nullptr
   const uint64_t* E = nullptr;   // all K decay bits, or nullptr: search W with a logarithm
+  uint64_t elast = 0;            // E[K - 1]
   __device__ __forceinline__ uint64_t w(int64_t k) const { return k < nw ? sW[k] : __ldg(&W[k]); }
   __device__ __forceinline__ uint32_t d(int64_t k) const {
     return k < nnear ? sD[k] : __ldg(&disp[k]);
@@ -175,6 +176,7 @@ __device__ __forceinline__ int64_t next_candidate_e(const DevParams& P, const Ne
   if (s >= T.K - 1 || !P.switching) return T.K;
   const uint64_t tb = (uint64_t)__double_as_longlong(u53pos(wE) * __longlong_as_double(Es));
   if (tb >= kDecayMinBits) {
+    if (T.elast >= tb + 16ull) return T.K;  // surely no candidate left: the walk ends
     const int64_t k = T.lower_bound_e(s + 1, tb);
     const uint64_t ek = k < T.K ? T.e(k) : 0ull;
     bool certain = true;
@@ -252,7 +254,7 @@ __device__ __noinline__ bool survives_dd(const DevParams& P, double si0, double 
 
 // 1 - P_ij = -expm1(beta (V - Vmax)) of the pair (S_i at i, S_j at i + (dx, dy)) in FP64 from the
 // beta-scaled pair table t: x = a1 (S_i.S_j) - (S_i.a3 d)(S_j.d) - bvm, |x error| <= c0 +
-// 2^-52 |x| (c0 covers the roundings), then expm1_np (relative error kExpm1RelErr).
+// 2^-52 |x| (c0 covers the roundings), then expm1_np6 (relative error kExpm1RelErr6).
 // x itself is returned in *x.
 __device__ __forceinline__ double pair_keep64(const Sw64& t, const double* Si, const double* Sj,
                                               int32_t dx, int32_t dy, double* x) {
@@ -263,7 +265,7 @@ __device__ __forceinline__ double pair_keep64(const Sw64& t, const double* Si, c
   const double pb = Sj[0] * fx + Sj[1] * fy;
   const double b = fma(t.a1, ss, fma(-pa, pb, -t.bvm));  // c0 covers these two roundings
   *x = b;
-  return -expm1_np(b);
+  return -expm1_np6(b);
 }
 
 // The integer hazard A_k of list element k (only the double-double tests need it).
@@ -271,10 +273,16 @@ __device__ __forceinline__ uint64_t hazard_of(const NearTable& T, int64_t k) {
   return T.w(k) - (k > 0 ? T.w(k - 1) : 0ull);
 }
 
+// Bits of 2^-990: below it the survival test's relative margin is not formed from the exponent.
+constexpr long long kRelMinBits = 0x0210000000000000ll;
+
 // FP64 survival test u q < 1 - P_ij: x = beta (V - Vmax) from the beta-scaled pair table
-// (t, the sweep's Sw64 entry), 1 - P = -expm1_np(x), margin bound t.bsw (precomputed: |dx| <=
-// c0, expm1_np within kExpm1RelErr, q within 2^-50, two roundings; doubled).  u is exact.
-// `keep` receives the FP64 value of 1 - P (within its error bound whatever the decision).
+// (t, the sweep's Sw64 entry), 1 - P = -expm1_np6(x).  The error of mu = (1 - P) - u q is below
+// t.bsw / 4 (|dx| <= c0, q within 2^-50, two roundings; precomputed) plus 2^-31 (1 - P)
+// (expm1_np6); the test is certain when |mu| exceeds twice the larger of the two doubled parts,
+// i.e. both t.bsw and 2^-28 (1 - P), compared as ordered bit images (2^-28 (1 - P) by the
+// exponent field, for 1 - P >= 2^-990).  u is exact.  `keep` receives the FP64 value of 1 - P
+// (within its error bound whatever the decision).
 __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t, double q,
                                               const double* Si, const double* Sj, int32_t dx,
                                               int32_t dy, const NearTable& T, int64_t k,
@@ -283,10 +291,11 @@ __device__ __forceinline__ bool survives_fp64(const DevParams& P, const Sw64& t,
   const double pr = pair_keep64(t, Si, Sj, dx, dy, &xk);
   keep = pr;
   const double mu = pr - u1 * q;
-  // mu > bsw, mu < -bsw on ordered bit images (bsw > 0: ord(-bsw) = -ord(bsw) - 1)
-  const long long om = ord_bits(mu), ob = ord_bits(t.bsw);
-  if (om > ob) return true;
-  if (om < -ob - 1) return false;
+  // mu > lim, mu < -lim on ordered bit images (lim > 0: ord(-lim) = -ord(lim) - 1)
+  const long long pb = __double_as_longlong(pr);
+  const long long ob = max(ord_bits(t.bsw), pb - (28ll << 52)), om = ord_bits(mu);
+  if (pb >= kRelMinBits && om > ob) return true;
+  if (pb >= kRelMinBits && om < -ob - 1) return false;
   ++ghits;
   return survives_dd(P, Si[0], Si[1], Si[2], Sj[0], Sj[1], Sj[2], dx, dy, hazard_of(T, k), u1);
 }

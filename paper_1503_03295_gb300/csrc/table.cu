@@ -102,10 +102,11 @@ __global__ void k_xy(int32_t Lx, int32_t Ly, double D, double beta, double2* __r
   t.ay = (double)ay;
   t.bvm = bvm;
   t.c0 = c64 * (1.0 + 0x1p-20);
-  // survival test of the switch: mu = (1 - P) - u q with 1 - P = -expm1_np(x): |d(1 - P)| <=
-  // |dx| + eps_z <= c0 + kExpm1RelErr; q (CUDA expm1 of a rounded 2 beta Vmax) within 2^-50;
-  // the product u q and the difference 2^-52 each.  Doubled.
-  t.bsw = 2.0 * (c64 + kExpm1RelErr + 0x1p-49) * (1.0 + 0x1p-20);
+  // survival test of the switch: mu = (1 - P) - u q with 1 - P = -expm1_np6(x): |d(1 - P)| <=
+  // |dx| <= c0 plus the relative error of expm1_np6 (bounded at run time, see survives_fp64); q
+  // (CUDA expm1 of a rounded 2 beta Vmax) within 2^-50; the product u q and the difference 2^-52
+  // each.  Doubled, and doubled again for the test against the larger of the two parts.
+  t.bsw = 4.0 * (c64 + 0x1p-49) * (1.0 + 0x1p-20);
   sw64[q] = t;
   const double c32 = beta * (0x1p-16 * dc * (double)r2) + 0x1p-21 * bvm;
   sw32[q] = make_float4((float)a1, (float)a3, (float)bvm, (float)(c32 * (1.0 + 0x1p-20)));
