@@ -224,14 +224,15 @@ def algorithmic_bytes(k, M, p0, cache=False):
 
 
 def algorithmic_flops(k, cand):
-    """FP64 operations per spin update of the FP64 form, planning figures: 70 per switching
-    candidate (one logarithm, one expm1, the pair energy) and, per pair endpoint of the sweep,
-    two pair energies (20) and the pseudointeraction term of the proposed spin (50, a log1mexp
-    counted as two transcendentals): the old spin's term is read from the pair cache, which the
-    switch filled, so 70 (120 without the cache); the colouring has none.  The kernels issue
-    fewer (about 40 per candidate, 39.5 per pair endpoint: see SWEEP64_EXECUTED_FP64_PER_PAIR),
-    so these fractions measure work done against the plan."""
-    return {"switch": 70.0 * cand, "colour": 0.0, "sweep": 70.0 * k}
+    """FP64 operations per spin update of the FP64 form, planning figures: 51 per switching
+    candidate (the pair energy 30, one expm1 20, and one multiply for the candidate search on
+    the table of decay values, which takes the place of a logarithm) and, per pair endpoint of
+    the sweep, two pair energies (20) and the pseudointeraction term of the proposed spin (50, a
+    log1mexp counted as two transcendentals): the old spin's term is read from the pair cache,
+    which the switch filled, so 70 (120 without the cache); the colouring has none.  The kernels
+    issue fewer (about 26 per candidate, 39.5 per pair endpoint: see
+    SWEEP64_EXECUTED_FP64_PER_PAIR), so these fractions measure work done against the plan."""
+    return {"switch": 51.0 * cand, "colour": 0.0, "sweep": 70.0 * k}
 
 
 def phase_ms(ph):

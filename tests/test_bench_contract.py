@@ -61,7 +61,7 @@ def test_algorithmic_work_figures():
     assert f["colour"] == 0.0
     # the sweep's plan per pair endpoint: two pair energies and one pseudointeraction term (the
     # other is read from the pair cache)
-    assert abs(f["switch"] - 70 * 14.4) < 1e-9 and abs(f["sweep"] - 70 * k) < 1e-9
+    assert abs(f["switch"] - 51 * 14.4) < 1e-9 and abs(f["sweep"] - 70 * k) < 1e-9
 
 
 def test_cooling_schedule_and_cell_splits():
