@@ -80,9 +80,10 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 5 : 4) k_switch(const DevPara
       pool_n -= take;
       need = __ballot_sync(0xffffffffu, !active);
     }
-    if (__ballot_sync(0xffffffffu, active) == 0u) break;
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (act == 0u) break;
     if (active && !walk_step<PREC>(P, T, Wtot, sw64, xyq, xy32, s, s32, epoch, mnn0, mnn1, o,
-                                   a, n_dip, ghits, g32)) {
+                                   a, n_dip, ghits, g32, act)) {
       const uint32_t n_out = walk_end<PREC>(P, mnn0, mnn1, o, a);
       b.hcnt[a.i] = n_out;
       n_half += n_out;

@@ -421,7 +421,11 @@ __device__ __forceinline__ void walk_begin(const DevParams& P, const NearTable& 
 }
 
 // Draws the next candidate of the walk and, if it lies on the lattice, tests its survival
-// (emitting the pair if it survives).  Returns false once the list is exhausted.
+// (emitting the pair if it survives).  Returns false once the list is exhausted.  sync_mask:
+// the lanes of the warp that run this step together (0 when threads walk independently); they
+// meet after the candidate search, whose loops run for different lengths (a far candidate
+// searches the list in global memory), so that the FP64 survival test is issued once for all of
+// them instead of once per group of lanes that left the search together.
 template <int PREC>
 __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T, uint64_t Wtot,
                                           const Sw64* __restrict__ sw,
@@ -431,7 +435,7 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
                                           const float4* __restrict__ s32, uint32_t epoch,
                                           int32_t mnn0, int32_t mnn1, const SwitchOut& o,
                                           SiteWalk<PREC>& a, unsigned long long& n_dip,
-                                          unsigned& ghits, unsigned& g32) {
+                                          unsigned& ghits, unsigned& g32, unsigned sync_mask) {
   if ((a.n & 1u) == 0u)
     a.w = philox((uint64_t)a.i, epoch, (uint64_t)(a.n >> 1), kTagSwitch, P.key0, P.key1);
   const uint64_t wE = (a.n & 1u) ? a.w.w[2] : a.w.w[0];
@@ -441,6 +445,7 @@ __device__ __forceinline__ bool walk_step(const DevParams& P, const NearTable& T
   const int64_t k = PREC == 1 ? next_candidate_fp32(P, T, a.sidx, a.Ws, Wtot, wE, g32, ghits)
                     : decay   ? next_candidate_e(P, T, a.sidx, a.Ws, Wtot, wE, ghits)
                               : next_candidate(P, T, a.sidx, a.Ws, Wtot, wE, ghits);
+  if (sync_mask) __syncwarp(sync_mask);
   if (k >= P.K) return false;
   const uint32_t d = T.d(k);
   const int32_t dx = (int16_t)(d & 0xFFFFu), dy = (int32_t)(d >> 16);
@@ -501,7 +506,7 @@ __device__ __forceinline__ uint32_t switch_site(const DevParams& P, const NearTa
   SiteWalk<PREC> a;
   walk_begin<PREC>(P, T, s, s32, i, id, a);
   while (walk_step<PREC>(P, T, Wtot, sw, xyq, xy32, s, s32, epoch, mnn0, mnn1, o, a, n_dip,
-                         ghits, g32)) {
+                         ghits, g32, 0u)) {
   }
   return walk_end<PREC>(P, mnn0, mnn1, o, a);
 }
