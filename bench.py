@@ -182,8 +182,8 @@ FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal: context
 # FP64 sweep kernels, per pair of the switched graph and per spin update, from one ncu capture
 # of the current kernels on a smaller lattice at T = 0.6 D (DRAM bytes and executed FP64
 # thread-instructions scale with the updates and pairs, not with L): see the named profile
-SWEEP64_EXECUTED_FP64_PER_PAIR = 39.5  # k_propose + k_sweep + k_resolve, thread-instructions
-SWEEP64_DRAM_BYTES_PER_UPDATE = 2652.0  # dram__bytes_read.sum + dram__bytes_write.sum
+SWEEP64_EXECUTED_FP64_PER_PAIR = 35.1  # k_propose + k_sweep + k_resolve, thread-instructions
+SWEEP64_DRAM_BYTES_PER_UPDATE = 2343.0  # dram__bytes_read.sum + dram__bytes_write.sum
 SWEEP64_TRAFFIC_T = 0.6
 SWEEP64_EXECUTED_SOURCE = "profiles/k_sweep_fp64_L1024_T0.6.md"
 
@@ -230,7 +230,7 @@ def algorithmic_flops(k, cand):
     the sweep, two pair energies (20) and the pseudointeraction term of the proposed spin (50, a
     log1mexp counted as two transcendentals): the old spin's term is read from the pair cache,
     which the switch filled, so 70 (120 without the cache); the colouring has none.  The kernels
-    issue fewer (about 26 per candidate, 39.5 per pair endpoint: see
+    issue fewer (about 26 per candidate, 35.1 per pair endpoint: see
     SWEEP64_EXECUTED_FP64_PER_PAIR), so these fractions measure work done against the plan."""
     return {"switch": 51.0 * cand, "colour": 0.0, "sweep": 70.0 * k}
 
