@@ -307,6 +307,7 @@ sco_status do_colour(sco_ctx* c) {
     SCO_TRY(cudaMalloc(&c->cb.cursor, (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.dcnt, (cap + 1) * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.bcnt, (size_t)32 * (cap + 1) * sizeof(uint32_t)));
+    if (!c->cb.boff) SCO_TRY(cudaMalloc(&c->cb.boff, (size_t)kKwSplitBlocks * 64 * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.tile_cnt, tc * sizeof(uint32_t)));
     SCO_TRY(cudaMalloc(&c->cb.scan_tmp, scan_tmp_bytes(tc > cap + 1 ? tc : cap + 1)));
     c->cls_cap = cap;
@@ -358,6 +359,7 @@ void free_all(sco_ctx* c) {
   cudaFree(c->cb.tile_cnt);
   cudaFree(c->cb.scan_tmp);
   cudaFree(c->cb.bcnt);
+  cudaFree(c->cb.boff);
   cudaFree(c->cb.meta);
   cudaFree(c->cb.imask);
   cudaFree(c->cb.imeta);

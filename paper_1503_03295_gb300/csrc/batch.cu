@@ -592,7 +592,7 @@ int batch_kw_occupancy(int schedule, int R, unsigned pal) {
   int n = 0;
   const cudaError_t e =
       schedule == 0 && pal <= kBcrMaxPalette
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_kw_bcr, 256, kw_bcr_smem(R, pal))
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_kw_bcr<false>, 256, kw_bcr_smem(R, pal))
           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_kw_level, 256, kw_smem(R));
   if (e != cudaSuccess || n < 1) n = 1;
   return n;
@@ -710,7 +710,7 @@ cudaError_t batch_colour(const BatchDev& B, const BatchLaunch& L, cudaStream_t s
     V.ilist = B.ilist;
     V.gmax = &B.ctl->gmax;
     V.low_gmax = low_gmax;
-    if ((e = launch_coop(k_kw_bcr, (unsigned)L.kw_grid, 256, kw_bcr_smem(B.R, B.pal_cap), st,
+    if ((e = launch_coop(k_kw_bcr<false>, (unsigned)L.kw_grid, 256, kw_bcr_smem(B.R, B.pal_cap), st,
                          V)) != cudaSuccess)
       return e;
     ++*L.launches;

@@ -322,6 +322,11 @@ cudaError_t low_setup(uint32_t gcap, int* blocks_per_sm, uint32_t* ecap) {
 
 }  // namespace
 
+// The split record build: row entries read per chunk, and the blocks per SM its registers
+// are held to (16 and 4 measured best at L = 2304: colour 7.35 ms per step, against 7.45 for 8
+// and 6 and 7.83 for 8 and 8, and 7.54 with the records built inside the cooperative kernel).
+constexpr int kRecChunk = 16, kRecBlocks = 4;
+
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
                    uint32_t g, int variant, ColourBufs& b, DevCounters* cnt,
                    unsigned long long ns_limit, cudaStream_t st, int64_t* launches) {
@@ -376,10 +381,18 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
   if (N >= (1 << 20) && g <= kBcrMaxPalette && M < kBcrMaxLevels) {
     const size_t sh = kw_bcr_smem(1, g);
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_kw_bcr, 256, sh);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_kw_bcr<false>, 256, sh);
     if (e != cudaSuccess) return e;
     if (bps > 4) bps = 4;
     if (bps < 1) bps = 1;
+    static int qbps = 0;  // the buckets-only instance
+    if (qbps == 0) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qbps, k_kw_bcr<true>, 256, sh)) !=
+          cudaSuccess)
+        return e;
+      if (qbps > kBcrBucketBlocks) qbps = kBcrBucketBlocks;
+      if (qbps < 1) qbps = 1;
+    }
     if ((e = cudaMemsetAsync(b.bcnt, 0, (size_t)kBcrMaxLevels * g * sizeof(uint32_t), st)) !=
         cudaSuccess)
       return e;
@@ -411,10 +424,34 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     // threads' polling slows the recolouring ones)
     V.free_max = 0;
     void* args[] = {(void*)&V};
-    e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr, dim3((unsigned)(bps * num_sms())),
-                                    dim3(256), args, sh, st);
-    if (e != cudaSuccess) return e;
-    ++*launches;
+    static int rbps = 0;
+    if (rbps == 0) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &rbps, k_kw_rec<kRecChunk, kRecBlocks>, 256, 0)) != cudaSuccess)
+        return e;
+      if (rbps < 1) rbps = 1;
+    }
+    const int64_t sgrid = std::min<int64_t>((int64_t)rbps * num_sms(), kKwSplitBlocks);
+    if (b.boff && g <= kLowMaxPal) {
+      // per level: the records in two plain launches (k_kw_hist reserves, k_kw_rec builds),
+      // then the cooperative kernel runs that level's buckets alone
+      for (unsigned p = low + 1; p <= M; ++p) {
+        k_kw_hist<<<(unsigned)sgrid, 256, 0, st>>>(V, p, b.boff);
+        k_kw_rec<kRecChunk, kRecBlocks><<<(unsigned)sgrid, 256, 0, st>>>(V, p, b.boff);
+        V.p_only = p;
+        V.prebuilt = 1;
+        e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr<true>,
+                                        dim3((unsigned)(qbps * num_sms())), dim3(256), args, sh,
+                                        st);
+        if (e != cudaSuccess) return e;
+        *launches += 3;
+      }
+    } else {
+      e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr<false>,
+                                      dim3((unsigned)(bps * num_sms())), dim3(256), args, sh, st);
+      if (e != cudaSuccess) return e;
+      ++*launches;
+    }
     k_kw_final<<<nb, 256, 0, st>>>(N, M, g, variant, b.word, b.colour, cnt);
     ++*launches;
     return cudaGetLastError();

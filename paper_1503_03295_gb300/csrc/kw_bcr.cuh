@@ -53,9 +53,14 @@ struct KwView {
   // buckets of at most this many vertices (record path) run without grid barriers between
   // them, each item waiting for its listed larger neighbours; 0: a quarter of the grid
   uint32_t free_max;
+  // split record build (one lattice): run level p_only alone (0: every level), and with
+  // prebuilt its buckets, list and records come from k_kw_hist and k_kw_rec
+  unsigned p_only;
+  int prebuilt;
 };
 
 constexpr int kItemList = kKwItemList;
+constexpr int kBcrBucketBlocks = 3;  // 4 (64 registers, more spills) measured slower
 constexpr int kItemChunk = 16;  // listed neighbours loaded together
 constexpr uint32_t kItemSlow = 0x100;
 
@@ -72,7 +77,8 @@ __device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t* p) {
 // still holds its value from level p - 1: left-half same-group neighbours go into the mask
 // (their colours are final at this level), right-half ones of larger previous colour into the
 // list; smaller ones are ignored (they keep colours >= g while gv's bucket runs).  Palettes
-// of at most 64 colours.
+// of at most 64 colours.  The row is read kChunk entries at a time.
+template <int kChunk = 16>
 __device__ __forceinline__ void kw_item_build(const KwView& V, uint32_t pos, uint32_t gv,
                                               uint32_t base, uint32_t c, unsigned p,
                                               const RepPlan& pl) {
@@ -85,18 +91,18 @@ __device__ __forceinline__ void kw_item_build(const KwView& V, uint32_t pos, uin
   unsigned long long mask = 0;
   uint32_t n = 0;
   uint32_t* out = V.ilist + (size_t)pos * kItemList;
-  for (uint32_t q0 = b; q0 < e; q0 += 16) {
-    uint32_t uu[16], cc[16];
+  for (uint32_t q0 = b; q0 < e; q0 += kChunk) {
+    uint32_t uu[kChunk], cc[kChunk];
 #pragma unroll
-    for (int a = 0; a < 16; ++a) uu[a] = q0 + a < e ? (V.col[q0 + a] & kIndexMask) : kNone;
+    for (int a = 0; a < kChunk; ++a) uu[a] = q0 + a < e ? (V.col[q0 + a] & kIndexMask) : kNone;
 #pragma unroll
-    for (int a = 0; a < 16; ++a) {  // offsets inside the group (>= gsz: another group)
+    for (int a = 0; a < kChunk; ++a) {  // offsets inside the group (>= gsz: another group)
       cc[a] = 0;
       uu[a] = uu[a] - lo;
       if (uu[a] < gsz) cc[a] = ld_relaxed_u8(&col8[lo + uu[a]]);
     }
 #pragma unroll
-    for (int a = 0; a < 16; ++a) {
+    for (int a = 0; a < kChunk; ++a) {
       if (uu[a] >= gsz) continue;
       const uint32_t cu = cc[a];
       if (uu[a] < half) {
@@ -271,7 +277,10 @@ inline size_t kw_bcr_smem(int R, unsigned pal) {
   return (size_t)(3 * R + 2 + 4 * pal + 1) * sizeof(uint32_t);
 }
 
-__global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
+// kBuckets: an instance that only runs the buckets of levels whose records the split kernels
+// built (V.prebuilt set), held to fewer registers for more resident threads per bucket.
+template <bool kBuckets>
+__global__ void __launch_bounds__(256, kBuckets ? kBcrBucketBlocks : 3) k_kw_bcr(const KwView V) {
   __shared__ int s_halt;
   if (threadIdx.x == 0) s_halt = V.halt ? ld_status(V.halt) : 0;
   __syncthreads();
@@ -291,9 +300,11 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
   const uint32_t nth = gridDim.x * blockDim.x;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
   // records (instead of rows) when every palette fits a 64-bit mask
-  const bool fast = V.imask != nullptr && V.col8 != nullptr && (V.gmax ? *V.gmax : pal) <= 64u;
+  const bool fast =
+      kBuckets || (V.imask != nullptr && V.col8 != nullptr && (V.gmax ? *V.gmax : pal) <= 64u);
   bool ok = true;
   for (unsigned p = 1; p <= V.levels && ok; ++p) {
+    if (V.p_only != 0 && p != V.p_only) continue;
     // right-half slots of every lattice at level p
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
       const RepPlan pl = V.plan[r];
@@ -325,6 +336,11 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
       return v < sbase[r + 1] - sbase[r] ? sbase[r] + v : kNone;
     };
     uint32_t* bc = V.bcnt + (size_t)p * pal;
+    if (kBuckets || V.prebuilt) {
+      for (unsigned c = threadIdx.x; c < pal; c += blockDim.x) start[c] = ld_u32_gpu(&bc[c]);
+      __syncthreads();
+      block_scan_excl(start, (int)pal);
+    } else {
     // bucket sizes: block histograms, then one reservation per (block, colour)
     for (uint32_t slot = gtid; slot < Rtot; slot += nth) {
       const uint32_t gv = vertex_of(slot);
@@ -358,6 +374,7 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
     if (!grid_sync(V.bar, V.status, V.ns_limit)) {
       ok = false;
       break;
+    }
     }
     // buckets from the largest previous colour down, one grid barrier apart.  Between its
     // arrival at a barrier and its wait, each thread fetches the row of its first item of the
@@ -481,6 +498,65 @@ __global__ void __launch_bounds__(256, 3) k_kw_bcr(const KwView V) {
     __syncthreads();
     for (int r = threadIdx.x; r < R; r += blockDim.x)
       if (smax[r]) atomicMax(&V.cnt[r].lev_rounds[p & 31], smax[r]);
+  }
+}
+
+// Split record build of level p for one lattice (V.R == 1), ahead of a k_kw_bcr launch that
+// runs only that level's buckets.  Both kernels deal the right-half slots to their threads in
+// the same grid-stride order, so that the reservation each block of k_kw_hist makes per colour
+// is where k_kw_rec puts that block's items; inside a (block, colour) range the order is free
+// (a bucket's vertices share a colour, hence no edge).  A plain launch with more resident
+// threads than the cooperative kernel keeps more records' load chains in flight.
+__device__ __forceinline__ uint32_t kw_split_slots(const RepPlan& pl, uint32_t N, unsigned p) {
+  const unsigned long long gsz = (unsigned long long)pl.g << p;
+  return (uint32_t)(((unsigned long long)N + gsz - 1) / gsz * ((unsigned long long)pl.g << (p - 1)));
+}
+
+__global__ void __launch_bounds__(256) k_kw_hist(const KwView V, unsigned p,
+                                                 uint32_t* __restrict__ boff) {
+  __shared__ uint32_t hist[kLowMaxPal];
+  const RepPlan pl = V.plan[0];
+  const uint32_t N = V.site_start[1] - V.site_start[0];
+  const unsigned pal = V.pal;
+  for (unsigned c = threadIdx.x; c < pal; c += blockDim.x) hist[c] = 0;
+  __syncthreads();
+  const uint32_t Rtot = kw_split_slots(pl, N, p), nth = gridDim.x * blockDim.x;
+  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < Rtot; slot += nth) {
+    const uint32_t v = kw_vertex(slot, pl.g << (p - 1), p, pl.magic);
+    if (v < N) atomicAdd(&hist[V.col8[v]], 1u);
+  }
+  __syncthreads();
+  uint32_t* bc = V.bcnt + (size_t)p * pal;
+  for (unsigned c = threadIdx.x; c < pal; c += blockDim.x)
+    boff[(size_t)blockIdx.x * pal + c] = hist[c] ? atomicAdd(&bc[c], hist[c]) : 0u;
+}
+
+template <int kChunk, int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) k_kw_rec(const KwView V, unsigned p,
+                                                            const uint32_t* __restrict__ boff) {
+  __shared__ uint32_t start[kLowMaxPal + 1];
+  __shared__ uint32_t lcur[kLowMaxPal];
+  const RepPlan pl = V.plan[0];
+  const uint32_t N = V.site_start[1] - V.site_start[0];
+  const unsigned pal = V.pal;
+  const uint32_t* bc = V.bcnt + (size_t)p * pal;
+  for (unsigned c = threadIdx.x; c < pal; c += blockDim.x) {
+    start[c] = bc[c];
+    lcur[c] = 0;
+  }
+  __syncthreads();
+  block_scan_excl(start, (int)pal);
+  for (unsigned c = threadIdx.x; c < pal; c += blockDim.x)
+    start[c] += boff[(size_t)blockIdx.x * pal + c];
+  __syncthreads();
+  const uint32_t Rtot = kw_split_slots(pl, N, p), nth = gridDim.x * blockDim.x;
+  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < Rtot; slot += nth) {
+    const uint32_t v = kw_vertex(slot, pl.g << (p - 1), p, pl.magic);
+    if (v >= N) continue;
+    const uint32_t c = V.col8[v];
+    const uint32_t pos = start[c] + atomicAdd(&lcur[c], 1u);
+    V.list[pos] = v;
+    kw_item_build<kChunk>(V, pos, v, 0u, c, p, pl);
   }
 }
 

@@ -132,8 +132,11 @@ struct ColourBufs {
   uint32_t* meta;    // 6 words: one-lattice view of the persistent colouring kernel
   unsigned long long* imask;  // N per-level vertex records of the colouring kernel
   uint32_t* imeta;            // N
-  uint32_t* ilist;            // 8 N (kItemList per record)
+  uint32_t* ilist;            // 32 N (kItemList per record)
+  uint32_t* boff;             // kKwSplitBlocks x 64: per (block, colour) bucket offsets of the
+                              // split record build (null: records built inside k_kw_bcr)
 };
+constexpr int kKwSplitBlocks = 2048;
 constexpr uint32_t kMaxStablePalette = 12288;  // palettes up to this size get stable classes
 constexpr int64_t kClassTileSites = 2048;
 // ns_limit: bound of every device-side wait of the colouring kernels (SCO_ETIMEOUT after it)
