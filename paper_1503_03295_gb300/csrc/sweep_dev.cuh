@@ -35,7 +35,9 @@ constexpr int kScale32 = 60;
 
 // Pair terms from the sweep table entry (Sw64): the beta-scaled field of S_j on site i,
 // f = a1 S_j - (S_j . a3 d) d, gives x = S.f - bvm = beta V(S) - beta Vmax for the old and the
-// new spin.
+// new spin (7 + 2 x 3 FP64 operations); where only the proposed spin's term is formed (the pair
+// cache holds the old one), x = a1 (S'.S_j) - (S_j.a3 d)(S'.d) - bvm takes 9.  Either way the
+// rounding stays far inside c0.
 //
 // Error bound of the margin mu = ln u + beta dE' (first order, doubled):
 //   per pair, |dx| <= c0 + eps_r |x|, and c0 from the table already includes eps_r 2 beta Vmax;
@@ -176,11 +178,11 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
     // {1 - P, x} of the pair at the old spin: one 16-byte read of the record's sector
     const double2 kv = reinterpret_cast<const double2*>(&pc.keep[h])[uj == 2u ? 1 : 0];
     const double zo = kv.x, xo = kv.y;
+    // x = a1 (S'.S_j) - (S_j.a3 d)(S'.d) - bvm for the proposed spin S'
+    const double ns = N0 * bx + N1 * by + N2 * bz;
     const double tp = bx * ax3 + by * ay3;
-    const double gx = a1 * bx - tp * fx;
-    const double gy = a1 * by - tp * fy;
-    const double gz = a1 * bz;
-    const double xn = fma(N0, gx, fma(N1, gy, fma(N2, gz, -bvm)));
+    const double nd = N0 * fx + N1 * fy;
+    const double xn = fma(a1, ns, fma(-tp, nd, -bvm));
     const bool okn = neg_strict(xn);
     const double zn = okn ? -expm1_np6(xn) : -1.0;
     if (uj == 0u) reinterpret_cast<double2*>(&pc.keep[h])[1] = make_double2(zn, xn);
@@ -506,11 +508,10 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
     const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
     const double2 kv = reinterpret_cast<const double2*>(&pc.keep[h])[uj == 2u ? 1 : 0];
     const double zo = kv.x, xo = kv.y;
+    const double ns = c.Sn[0] * bx + c.Sn[1] * by + c.Sn[2] * bz;
     const double tp = bx * ax3 + by * ay3;
-    const double gx = t.a1 * bx - tp * fx;
-    const double gy = t.a1 * by - tp * fy;
-    const double gz = t.a1 * bz;
-    const double xn = fma(c.Sn[0], gx, fma(c.Sn[1], gy, fma(c.Sn[2], gz, -t.bvm)));
+    const double nd = c.Sn[0] * fx + c.Sn[1] * fy;
+    const double xn = fma(t.a1, ns, fma(-tp, nd, -t.bvm));
     const bool okn = neg_strict(xn);
     const double zn = okn ? -expm1_np6(xn) : -1.0;
     if (uj == 0u) reinterpret_cast<double2*>(&pc.keep[h])[1] = make_double2(zn, xn);
