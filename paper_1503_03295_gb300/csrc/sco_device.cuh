@@ -221,6 +221,20 @@ __device__ __forceinline__ double log_np(double x) {
   return fma(kd, kLogLn2Hi, lh) + (lp + fma(kd, kLogLn2Lo, ll));
 }
 __device__ __forceinline__ double expm1_np6(double x) { return expm1_np_deg<6>(x); }
+// -expm1_np6(x) formed directly: -(s e + (s - 1)) = (1 - s) - s e is one FMA with the sign folded
+// into its operands; round to nearest is symmetric, so the value is exactly -expm1_np6(x) (one
+// FP64 negation fewer where the term is stored and multiplied).
+__device__ __forceinline__ double neg_expm1_np6(double x) {
+  const double t = fma(x, kExpInvLn2, 0x1.8p52);
+  const double kd = t - 0x1.8p52;
+  const int k = max(__double2loint(t), -1000);
+  const double r = fma(-kd, kExpLn2, x);
+  const double e = r * expm1_poly6(r);
+  const double s = __longlong_as_double((long long)(1023 + k) << 52);
+  const double res = fma(-s, e, 1.0 - s);
+  const long long xb = __double_as_longlong(x);
+  return (xb < 0 && (xb & 0x7FFFFFFFFFFFFFFFll) > 0x4044000000000000ll) ? 1.0 : res;
+}
 
 // Sweep constants of a pair at (|dx|, |dy|) for the FP64 decisions (64 bytes).  With the
 // signs of (dx, dy) applied to a3x, a3y, ax, ay, the field of S_j on site i scaled by beta is

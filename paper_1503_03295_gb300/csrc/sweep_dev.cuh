@@ -86,7 +86,7 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     const double xn = fma(N0, gx, fma(N1, gy, fma(N2, gz, -bvm)));
     const double xo = fma(S0, gx, fma(S1, gy, fma(S2, gz, -bvm)));
     if (!neg_strict(xn) || !neg_strict(xo)) return 2;
-    const double zn = -expm1_np6(xn), zo = -expm1_np6(xo);
+    const double zn = neg_expm1_np6(xn), zo = neg_expm1_np6(xo);
     pz_n *= zn;
     pz_o *= zo;
     if (pos_bits(pz_n) < small_b) { pz_n *= 0x1p600; ++sc_n; }
@@ -184,7 +184,7 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
     const double nd = N0 * fx + N1 * fy;
     const double xn = fma(a1, ns, fma(-tp, nd, -bvm));
     const bool okn = neg_strict(xn);
-    const double zn = okn ? -expm1_np6(xn) : -1.0;
+    const double zn = okn ? neg_expm1_np6(xn) : -1.0;
     if (uj == 0u) reinterpret_cast<double2*>(&pc.keep[h])[1] = make_double2(zn, xn);
     else if (pc.carry) pc.keepl[h] = make_double2(zn, xn);
     // the cached term must be a positive number (a non-positive one marks an FP64 evaluation
@@ -430,7 +430,7 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
       bad = 1;
       continue;
     }
-    const double zn = -expm1_np6(xn), zo = -expm1_np6(xo);
+    const double zn = neg_expm1_np6(xn), zo = neg_expm1_np6(xo);
     pz_n *= zn;
     pz_o *= zo;
     if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
@@ -513,7 +513,7 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
     const double nd = c.Sn[0] * fx + c.Sn[1] * fy;
     const double xn = fma(t.a1, ns, fma(-tp, nd, -t.bvm));
     const bool okn = neg_strict(xn);
-    const double zn = okn ? -expm1_np6(xn) : -1.0;
+    const double zn = okn ? neg_expm1_np6(xn) : -1.0;
     if (uj == 0u) reinterpret_cast<double2*>(&pc.keep[h])[1] = make_double2(zn, xn);
     else if (pc.carry) pc.keepl[h] = make_double2(zn, xn);
     if (!okn || !neg_strict(xo) || !(pos_bits(zo) - 1ull < 0x7FEFFFFFFFFFFFFFull)) {

@@ -265,7 +265,7 @@ __device__ __forceinline__ double pair_keep64(const Sw64& t, const double* Si, c
   const double pb = Sj[0] * fx + Sj[1] * fy;
   const double b = fma(t.a1, ss, fma(-pa, pb, -t.bvm));  // c0 covers these two roundings
   *x = b;
-  return -expm1_np6(b);
+  return neg_expm1_np6(b);
 }
 
 // The integer hazard A_k of list element k (only the double-double tests need it).
