@@ -28,8 +28,10 @@ struct SiteCtx {
 };
 
 // The pseudointeraction terms enter as sum_j [L_o,j - L_n,j] = log(prod z_o) - log(prod z_n)
-// with z = 1 - e^x = -expm1(x): one expm1 per pair energy and two logarithms per site.  The
-// products are renormalised by 2^kScale (exact) so that they never underflow.
+// with z = 1 - e^x = -expm1(x): one expm1 per pair energy and two logarithms per site (the
+// cached FP64 path compares the products instead: u prod z_o e^(sum dx) < prod z_n, see
+// accept_fp64_cached).  The products are renormalised by 2^kScale (exact) so that they never
+// underflow.
 constexpr int kScale64 = 600;
 constexpr int kScale32 = 60;
 
@@ -223,16 +225,37 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
     tex = -(P.beta * P.J) * dot;
     bex = 0x1p-44 * fabs(P.beta * P.J);
   }
-  const double lo = log_np(pz_o), ln = log_np(pz_n);
-  const double scale = (double)((sc_n - sc_o) * kScale64) * P.ln2_hi;
-  const double lu = log_np(c.u);
-  const double mu = lu + ((bdv + tex) + ((lo - ln) + scale));
+  // The decision in product form, without logarithms: mu < 0 is u Pz_o e^A < Pz_n with A = bdv +
+  // tex and Pz = pz 2^(-600 sc).  e^A = 2^k e^r, k = round(A / ln2) (|k| <= 2^20, else left
+  // undecided), e^r = 1 + r p(r) with p of expm1_np6 (relative error below 2^-32, the reduction's
+  // below 2^-34); X = u pz_o e^r and K = k + 600 (sc_n - sc_o), and X 2^K against pz_n is decided
+  // on the exponent fields when they differ by 2 or more, else by D = X 2^K - pz_n (X 2^K formed
+  // exactly from the bits).  delta bounds the relative errors of X 2^K and pz_n together,
+  // doubled: the terms of the logarithmic form's bound without its logarithms, and 2^-31 for e^r,
+  // its reduction, the two products and D.
+  const double A = bdv + tex;
+  const double t = fma(A, kExpInvLn2, 0x1.8p52);
+  const double kd = t - 0x1.8p52;
+  const int k = __double2loint(t);
+  if (k > (1 << 20) || k < -(1 << 20)) return 2;
+  const double r = fma(-kd, kExpLn2, A);
+  const double er = fma(r, expm1_poly6(r), 1.0);
+  const double X = (c.u * pz_o) * er;
   const double c0s = (double)n * __longlong_as_double((long long)c0m);
-  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
-                          kLogRelErr * (fabs(lo) + fabs(ln) + fabs(lu)) + bex +
-                          0x1p-51 * (fabs(scale) + fabs(tex) + fabs(bdv) + fabs(mu)));
-  if (mu < -B) return 1;
-  if (mu > B) return 0;
+  const double delta = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin +
+                              n * (4.0 * kExpm1RelErr6 + 0x1p-51) + bex +
+                              0x1p-51 * (fabs(tex) + fabs(bdv)) + 0x1p-31);
+  if (!(delta < 0.25)) return 2;
+  const int eX = exp_field(X), eY = exp_field(pz_n);
+  if (eX == 0) return 1;  // u = 0
+  const int dE = eX + k + kScale64 * (sc_n - sc_o) - eY;
+  if (dE >= 2) return 0;   // X 2^K >= 2^(eY + 2) > 2 pz_n
+  if (dE <= -2) return 1;  // X 2^K < 2^(eY - 1) <= pz_n / 2
+  const double Xs = __longlong_as_double(__double_as_longlong(X) + ((long long)(dE + eY - eX) << 52));
+  const double D = Xs - pz_n;
+  const long long oD = ord_bits(D), ol = ord_bits(delta * pz_n);
+  if (oD < -ol - 1) return 1;  // D < -delta pz_n
+  if (oD > ol) return 0;       // D > delta pz_n
   return 2;
 }
 
