@@ -197,8 +197,18 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
     }
     pz_n *= zn;
     pz_o *= zo;
-    if (pos_bits(pz_n) < small_b) { pz_n *= 0x1p600; ++sc_n; }
-    if (pos_bits(pz_o) < small_b) { pz_o *= 0x1p600; ++sc_o; }
+    // renormalised by 2^600 on the exponent field (a product below 2^-600 of factors above
+    // 2^-400 is normal; a subnormal one leaves the decision to the exact path)
+    if (pos_bits(pz_n) < small_b) {
+      bad |= exp_field(pz_n) == 0;
+      pz_n = __longlong_as_double(__double_as_longlong(pz_n) + (600ll << 52));
+      ++sc_n;
+    }
+    if (pos_bits(pz_o) < small_b) {
+      bad |= exp_field(pz_o) == 0;
+      pz_o = __longlong_as_double(__double_as_longlong(pz_o) + (600ll << 52));
+      ++sc_o;
+    }
     bdv += xn - xo;
     dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
     c0m = max(c0m, pos_bits(t.c0));
