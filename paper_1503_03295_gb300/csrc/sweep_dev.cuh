@@ -35,6 +35,18 @@ struct SiteCtx {
 constexpr int kScale64 = 600;
 constexpr int kScale32 = 60;
 
+// p by 2^600 on the exponent field when below 2^-600, counted in sc (a multiply would be issued
+// on every pair as a select); false for a subnormal or zero p (the decision then goes to the
+// exact path).
+__device__ __forceinline__ bool renorm600(double& p, int& sc) {
+  const unsigned long long b = pos_bits(p);
+  if (b >= 0x1A70000000000000ull) return true;  // 2^-600
+  if ((b >> 52) == 0) return false;
+  p = __longlong_as_double((long long)(b + (600ull << 52)));
+  ++sc;
+  return true;
+}
+
 // Pair terms from the sweep table entry (Sw64): the beta-scaled field of S_j on site i,
 // f = a1 S_j - (S_j . a3 d) d, gives x = S.f - bvm = beta V(S) - beta Vmax for the old and the
 // new spin (7 + 2 x 3 FP64 operations); where only the proposed spin's term is formed (the pair
@@ -65,7 +77,6 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
   double bdv = 0.0, pz_o = 1.0, pz_n = 1.0;
   unsigned long long c0m = 0;  // bits of the largest c0 (n max c0 bounds their sum)
   int dmax = -2046;  // largest e(c0_j) - e(z_j)
-  const unsigned long long small_b = pos_bits(0x1p-600);
   int sc_o = 0, sc_n = 0, n = 0;
   const uint32_t e1 = row_ptr[c.i + 1];
   for (uint32_t e = row_ptr[c.i]; e < e1; ++e) {
@@ -91,8 +102,7 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
     const double zn = neg_expm1_np6(xn), zo = neg_expm1_np6(xo);
     pz_n *= zn;
     pz_o *= zo;
-    if (pos_bits(pz_n) < small_b) { pz_n *= 0x1p600; ++sc_n; }
-    if (pos_bits(pz_o) < small_b) { pz_o *= 0x1p600; ++sc_o; }
+    if (!renorm600(pz_n, sc_n) || !renorm600(pz_o, sc_o)) return 2;
     bdv += xn - xo;
     dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
     c0m = max(c0m, pos_bits(t.c0));
@@ -159,7 +169,6 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
   double bdv = 0.0, pz_o = 1.0, pz_n = 1.0;
   unsigned long long c0m = 0;
   int dmax = -2046;
-  const unsigned long long small_b = pos_bits(0x1p-600);
   int sc_o = 0, sc_n = 0, n = 0;
   bool bad = false;
   const uint32_t e1 = row_ptr[c.i + 1];
@@ -197,18 +206,7 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
     }
     pz_n *= zn;
     pz_o *= zo;
-    // renormalised by 2^600 on the exponent field (a product below 2^-600 of factors above
-    // 2^-400 is normal; a subnormal one leaves the decision to the exact path)
-    if (pos_bits(pz_n) < small_b) {
-      bad |= exp_field(pz_n) == 0;
-      pz_n = __longlong_as_double(__double_as_longlong(pz_n) + (600ll << 52));
-      ++sc_n;
-    }
-    if (pos_bits(pz_o) < small_b) {
-      bad |= exp_field(pz_o) == 0;
-      pz_o = __longlong_as_double(__double_as_longlong(pz_o) + (600ll << 52));
-      ++sc_o;
-    }
+    if (!renorm600(pz_n, sc_n) || !renorm600(pz_o, sc_o)) bad = true;
     bdv += xn - xo;
     dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
     c0m = max(c0m, pos_bits(t.c0));
@@ -466,8 +464,7 @@ __device__ int accept_fp64_warp(const DevParams& P, const SiteCtx& c,
     const double zn = neg_expm1_np6(xn), zo = neg_expm1_np6(xo);
     pz_n *= zn;
     pz_o *= zo;
-    if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
-    if (pz_o < 0x1p-600) { pz_o *= 0x1p600; ++sc_o; }
+    if (!renorm600(pz_n, sc_n) || !renorm600(pz_o, sc_o)) bad = 1;
     bdv += xn - xo;
     dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
     c0s += t.c0;
@@ -555,8 +552,7 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
     }
     pz_n *= zn;
     pz_o *= zo;
-    if (pz_n < 0x1p-600) { pz_n *= 0x1p600; ++sc_n; }
-    if (pz_o < 0x1p-600) { pz_o *= 0x1p600; ++sc_o; }
+    if (!renorm600(pz_n, sc_n) || !renorm600(pz_o, sc_o)) bad = 1;
     bdv += xn - xo;
     dmax = max(dmax, exp_field(t.c0) - min(exp_field(zn), exp_field(zo)));
     c0s += t.c0;
