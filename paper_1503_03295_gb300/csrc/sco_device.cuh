@@ -167,7 +167,8 @@ __device__ __forceinline__ double pair_V(double Dc, double r2, double ax, double
 // The library's own expm1 for x <= 0.35, branch-free (a warp never runs two versions): x =
 // k ln2 + r with k = round(x / ln2) (by the 1.5 2^52 shift) and r = fma(-k, ln2, x),
 // expm1(r) = r p(r) (p of expm1_poly.h, interpolation error < 1e-13), expm1(x) =
-// fma(2^k, expm1(r), 2^k - 1), and -1 below x = -40 (e^x < 2^-57).  Relative error below
+// fma(2^k, expm1(r), 2^k - 1), which rounds to -1 exactly below x = -40 (e^x < 2^-57; k is
+// clamped at -1000 so that 2^k stays normal).  Relative error below
 // 2^-43: interpolation 2^-43.2; Horner <= gamma_16 p(|r|) / p(r) <= 23 u; r off by at most
 // |k| |ln2 - fl(ln2)| <= 58 x 2.3e-17; for k <= -1 the 2^k expm1(r) part (<= 0.42 2^k) carries
 // these while |expm1(x)| >= 0.29.  Stated as kExpm1RelErr = 2^-42; the FP64 decisions carry it
@@ -186,10 +187,9 @@ __device__ __forceinline__ double expm1_np_deg(double x) {
   const double r = fma(-kd, kExpLn2, x);
   const double e = r * (kDeg == 8 ? expm1_poly(r) : expm1_poly6(r));
   const double s = __longlong_as_double((long long)(1023 + k) << 52);
-  const double res = fma(s, e, s - 1.0);
-  // x < -40 from the bits: sign set and |x| bits above those of 40
-  const long long xb = __double_as_longlong(x);
-  return (xb < 0 && (xb & 0x7FFFFFFFFFFFFFFFll) > 0x4044000000000000ll) ? -1.0 : res;
+  // below x = -40 (k <= -58, s (1 + e) < 2^-57) this rounds to -1 exactly, the clamp of k keeping
+  // s normal; no select for that range (one FP64 instruction)
+  return fma(s, e, s - 1.0);
 }
 __device__ __forceinline__ double expm1_np(double x) { return expm1_np_deg<8>(x); }
 
@@ -231,9 +231,7 @@ __device__ __forceinline__ double neg_expm1_np6(double x) {
   const double r = fma(-kd, kExpLn2, x);
   const double e = r * expm1_poly6(r);
   const double s = __longlong_as_double((long long)(1023 + k) << 52);
-  const double res = fma(-s, e, 1.0 - s);
-  const long long xb = __double_as_longlong(x);
-  return (xb < 0 && (xb & 0x7FFFFFFFFFFFFFFFll) > 0x4044000000000000ll) ? 1.0 : res;
+  return fma(-s, e, 1.0 - s);
 }
 
 // Sweep constants of a pair at (|dx|, |dy|) for the FP64 decisions (64 bytes).  With the
