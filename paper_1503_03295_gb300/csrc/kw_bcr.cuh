@@ -60,8 +60,11 @@ struct KwView {
 };
 
 constexpr int kItemList = kKwItemList;
-constexpr int kBcrBucketBlocks = 3;  // 4 (64 registers, more spills) measured slower
-constexpr int kItemChunk = 16;  // listed neighbours loaded together
+// blocks per SM of the buckets-only instance (64 registers): with the overflow path out of line
+// and lists read 8 entries at a time, 4 blocks measured best at L = 2304 (colour 7.23 ms per step
+// against 7.42 for 3 blocks and 16 entries, 7.23 for 5 blocks)
+constexpr int kBcrBucketBlocks = 4;
+constexpr int kItemChunk = 8;  // listed neighbours loaded together
 constexpr uint32_t kItemSlow = 0x100;
 
 __device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t* p) {
@@ -116,6 +119,12 @@ __device__ __forceinline__ void kw_item_build(const KwView& V, uint32_t pos, uin
   V.imask[pos] = mask;
   V.imeta[pos] = n > (uint32_t)kItemList ? kItemSlow : n;
 }
+
+// An item whose record overflowed (more larger neighbours than it lists): recoloured from its
+// row, in a function of its own so that the row's registers stay out of the bucket loop.
+__device__ __noinline__ bool kw_item_slow(uint32_t gv, uint32_t base, uint32_t cb, unsigned p,
+                                          uint32_t g, unsigned long long magic, const KwView V,
+                                          unsigned& rm, unsigned long long t_start);
 
 // An item's record head, loaded ahead of its bucket (the list is read when it runs).
 struct KwItem {
@@ -277,6 +286,15 @@ inline size_t kw_bcr_smem(int R, unsigned pal) {
   return (size_t)(3 * R + 2 + 4 * pal + 1) * sizeof(uint32_t);
 }
 
+__device__ __noinline__ bool kw_item_slow(uint32_t gv, uint32_t base, uint32_t cb, unsigned p,
+                                          uint32_t g, unsigned long long magic, const KwView V,
+                                          unsigned& rm, unsigned long long t_start) {
+  KwRow w;
+  kw_fetch(w, gv, V.row_ptr, V.col);
+  return kw_recolour(gv - base, cb, w, p, g, magic, V.col, V.word + base, V.col8 + base, rm,
+                     V.status, t_start, V.ns_limit);
+}
+
 // kBuckets: an instance that only runs the buckets of levels whose records the split kernels
 // built (V.prebuilt set), held to fewer registers for more resident threads per bucket.
 template <bool kBuckets>
@@ -393,12 +411,8 @@ __global__ void __launch_bounds__(256, kBuckets ? kBcrBucketBlocks : 3) k_kw_bcr
         unsigned rm = 0;
         bool mine;
         if (it.meta & kItemSlow) {  // more larger neighbours than the record holds
-          const uint32_t base = sbase[r];
-          KwRow w;
-          kw_fetch(w, it.gv, V.row_ptr, V.col);
-          mine = kw_recolour(it.gv - base, (uint32_t)cb, w, p, V.plan[r].g, V.plan[r].magic,
-                             V.col, V.word + base, V.col8 + base, rm, V.status, t_start,
-                             V.ns_limit);
+          mine = kw_item_slow(it.gv, sbase[r], (uint32_t)cb, p, V.plan[r].g, V.plan[r].magic, V,
+                              rm, t_start);
         } else {
           mine = kw_item_recolour(it, V, p, rm, t_start);
         }
