@@ -90,8 +90,10 @@ def test_colouring_bit_exact(L, T, variant):
 
 
 @pytest.mark.parametrize("L,T,J,n", [(16, 0.5, 0.0, 200), (64, 0.3, 0.0, 20), (64, 1.2, 0.0, 20),
-                                     (32, 0.8, 1.0, 20)])
+                                     (32, 0.8, 1.0, 20), (32, 0.08, 0.0, 30)])
 def test_trajectory_bit_exact(L, T, J, n):
+    """FP64 form against the oracle step by step; T = 0.08 D (beta D = 12.5) drives the decision's
+    products below 2^-600 (their renormalisation) and its exponentials over a wide range."""
     g, o = _pair(L, T=T, J=J, D=1.0 if J == 0 else 0.1, seed=7)
     for k in range(n):
         g.sweep(1)
