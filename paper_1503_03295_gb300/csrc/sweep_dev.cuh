@@ -405,6 +405,25 @@ __device__ __forceinline__ void write_site(const DevParams& P, const SiteCtx& c,
   acc[c.i] = ok ? 1 : 0;
 }
 
+// Product over the warp of the lanes' p 2^(-600 sc) (p a positive normal double): mantissa m in
+// [1, 2) and exponent e on every lane (the butterfly multiplies the same pairs on both lanes of
+// a step, so all lanes end with the same bits).
+__device__ __forceinline__ void warp_prod(double p, int sc, double& m, int& e) {
+  const unsigned long long b = pos_bits(p);
+  e = (int)(b >> 52) - 1023 - kScale64 * sc;
+  m = __longlong_as_double((long long)((b & 0xFFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m *= __shfl_xor_sync(0xffffffffu, m, o);
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    const unsigned long long mb = pos_bits(m);
+    if ((mb >> 52) > 1023u) {  // m in [2, 4): halve it exactly
+      m = __longlong_as_double((long long)(mb - (1ull << 52)));
+      ++e;
+    }
+  }
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -558,10 +577,6 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
     c0s += t.c0;
     ++n;
   }
-  const double lo = log_np(pz_o) - (double)(sc_o * kScale64) * P.ln2_hi;
-  const double ln = log_np(pz_n) - (double)(sc_n * kScale64) * P.ln2_hi;
-  const double lsum = warp_sum_d(lo - ln);
-  const double labs = warp_sum_d(fabs(lo) + fabs(ln));
   bdv = warp_sum_d(bdv);
   c0s = warp_sum_d(c0s);
   dmax = __reduce_max_sync(0xffffffffu, dmax);
@@ -569,6 +584,10 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (bad) return 2;
   if (n > 0 && dmax + 2 + (32 - __clz(n)) > -10) return 2;
+  double mo, mn;
+  int eo, en;
+  warp_prod(pz_o, sc_o, mo, eo);
+  warp_prod(pz_n, sc_n, mn, en);
   const double lin = n > 0 && dmax + 2 >= -1022
                          ? (double)n * __longlong_as_double((long long)(dmax + 2 + 1023) << 52)
                          : 0.0;
@@ -588,13 +607,30 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
     tex = -(P.beta * P.J) * dot;
     bex = 0x1p-44 * fabs(P.beta * P.J);
   }
-  const double lu = log_np(c.u);
-  const double mu = lu + ((bdv + tex) + lsum);
-  const double B = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin + n * (4.0 * kExpm1RelErr6 + 0x1p-51) +
-                          kLogRelErr * (labs + fabs(lu)) + 0x1p-49 * labs + bex +
-                          0x1p-51 * (fabs(tex) + fabs(bdv) + fabs(mu)));
-  if (mu < -B) return 1;
-  if (mu > B) return 0;
+  // the product form of accept_fp64_cached on the warp's products mo 2^eo and mn 2^en (the
+  // butterfly's ten products add 2^-49 to the 2^-31 term)
+  const double A = bdv + tex;
+  const double t = fma(A, kExpInvLn2, 0x1.8p52);
+  const double kd = t - 0x1.8p52;
+  const int k = __double2loint(t);
+  if (k > (1 << 20) || k < -(1 << 20)) return 2;
+  const double r = fma(-kd, kExpLn2, A);
+  const double er = fma(r, expm1_poly6(r), 1.0);
+  const double X = (c.u * mo) * er;
+  const double delta = 2.0 * ((double)(n + 4) * c0s + 2.0 * lin +
+                              n * (4.0 * kExpm1RelErr6 + 0x1p-51) + bex +
+                              0x1p-51 * (fabs(tex) + fabs(bdv)) + 0x1p-31);
+  if (!(delta < 0.25)) return 2;
+  const int eX = exp_field(X);
+  if (eX == 0) return 1;  // u = 0
+  const int dE = eX - 1023 + k + eo - en;  // mn in [1, 2)
+  if (dE >= 2) return 0;
+  if (dE <= -2) return 1;
+  const double Xs = __longlong_as_double(__double_as_longlong(X) + ((long long)(dE + 1023 - eX) << 52));
+  const double D = Xs - mn;
+  const long long oD = ord_bits(D), ol = ord_bits(delta * mn);
+  if (oD < -ol - 1) return 1;
+  if (oD > ol) return 0;
   return 2;
 }
 
