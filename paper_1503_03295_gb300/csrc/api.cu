@@ -116,9 +116,9 @@ struct sco_ctx {
   bool colour_valid = false;
   uint32_t g = 1;
   uint64_t nnz = 0;
-  // FP64 form: the pair cache (hid parallel to col, keep arrays in SwitchBufs, upd per site);
-  // cache_state 0: keep holds the terms at the current spins; 1: carry from the last step's
-  // decisions first; 2: rebuild from the spins first
+  // FP64 form: the pair cache (hid parallel to col, keep records in SwitchBufs, upd per site);
+  // cache_state 0: the first halves hold the terms at the current spins; 1: the halves given by
+  // the parities of the last step hold them; 2: rebuild from the spins first
   uint32_t* hid = nullptr;
   uint8_t* upd = nullptr;
   int cache_state = 0;
@@ -205,21 +205,16 @@ bool cache_on(const sco_ctx* c) { return c->sw.keep != nullptr; }
 // The per-half-edge records of the pair cache for the current overflow capacity.
 cudaError_t alloc_keep(sco_ctx* c) {
   cudaFree(c->sw.keep);
-  cudaFree(c->sw.keepl);
   c->sw.keep = nullptr;
-  c->sw.keepl = nullptr;
   const size_t n = (size_t)c->P.N * kSlotCap + c->sw.ovf_cap;
-  cudaError_t e = cudaMalloc(&c->sw.keep, n * sizeof(double4_32a));
-  // the last endpoint's values are kept only when a graph serves several steps
-  if (e == cudaSuccess && c->p.n_sw > 1) e = cudaMalloc(&c->sw.keepl, n * sizeof(double2));
-  return e;
+  return cudaMalloc(&c->sw.keep, n * sizeof(double4_32a));
 }
 
 PairCache pair_cache(sco_ctx* c) {
   if (!cache_on(c)) return PairCache{};
   // the last endpoint's term is needed only when the next step keeps this graph
   const int carry = (c->t + 1) % c->p.n_sw != 0 ? 1 : 0;
-  return PairCache{c->hid, c->sw.keep, c->sw.keepl, c->upd, carry && c->sw.keepl ? 1 : 0};
+  return PairCache{c->hid, c->sw.keep, c->upd, carry, c->cache_state != 1 ? 1 : 0};
 }
 
 sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4* src32) {
@@ -248,9 +243,9 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4
       // half-edge ids must stay below 2^32 for the cache: else run without it
       if ((uint64_t)c->P.N * kSlotCap + need >= (1ull << 32)) {
         cudaFree(c->sw.keep);
-        cudaFree(c->sw.keepl);
         c->sw.keep = nullptr;
-        c->sw.keepl = nullptr;
+        cudaFree(c->hid);
+        c->hid = nullptr;
       } else {
         SCO_TRY(alloc_keep(c));
       }
@@ -266,7 +261,7 @@ sco_status do_switch(sco_ctx* c, uint32_t epoch, const double* src, const float4
     if (c->hcnt->ovf_n > c->sw.ovf_cap) return SCO_ECAPACITY;
   }
   c->nnz = c->hcnt->nnz;
-  if (cache_on(c) && c->hid && c->col_cap < c->nnz) {
+  if (c->col_cap < c->nnz) {
     cudaFree(c->hid);
     c->hid = nullptr;
   }
@@ -343,7 +338,6 @@ void free_all(sco_ctx* c) {
   cudaFree(c->sw.ovf);
   cudaFree(c->sw.scan_tmp);
   cudaFree(c->sw.keep);
-  cudaFree(c->sw.keepl);
   cudaFree(c->hid);
   cudaFree(c->upd);
   cudaFree(c->row_ptr);
@@ -494,9 +488,7 @@ sco_status sco_sweep(sco_ctx* c, int32_t n_mcs) {
     if (st != SCO_OK) return st;
     {
       PhaseTimer tm(c, kPhSweep);
-      if (cache_on(c) && c->cache_state == 1)
-        SCO_TRY(cache_carry_run(c->P, c->sw, c->cb.colour, c->upd, c->cnt, c->st, &c->launches));
-      else if (cache_on(c) && c->cache_state == 2)
+      if (cache_on(c) && c->cache_state == 2)
         SCO_TRY(cache_build_run(c->P, c->tab, c->s, c->sw, c->cnt, c->st, &c->launches));
       SCO_TRY(sweep_run(c->P, c->tab, c->s, c->s32, c->row_ptr, c->col, c->cb.perm, c->cb.off,
                         c->g, (uint64_t)c->t, c->p.precision, c->acc, c->defer, c->cb.dcnt,

@@ -89,12 +89,11 @@ struct SwitchBufs {
   uint64_t* scan_tmp;
   // FP64 form only (else null): the pair cache, one 32-byte record per half-edge id h (slot
   // i * kSlotCap + q of site i, then N * kSlotCap + overflow index), N * kSlotCap + ovf_cap of
-  // them: {1 - P_ij, x = beta (V - Vmax)} at the current spins, then the same two after the
-  // move of the endpoint that is decided first in the MC step (written by that endpoint
-  // whatever its decision), so that every access of a pair touches one sector; keepl (when the
-  // graph serves several steps): the same two after the move of the endpoint decided last.
+  // them, two halves of {1 - P_ij, x = beta (V - Vmax)}: one holds the pair at the current
+  // spins, the other the pair after the last proposed move of one endpoint (which half is which
+  // follows the endpoints' acceptance parities, see PairCache), so that every access of a pair
+  // touches one sector.  The switch writes the first half.
   double4_32a* keep;
-  double2* keepl;
 };
 cudaError_t switch_run(const DevParams& P, const Table& t, const double* s, const float4* s32,
                        int precision, uint32_t epoch, SwitchBufs& b, DevCounters* cnt,
@@ -150,11 +149,15 @@ cudaError_t bucket_run(const DevParams& P, uint32_t g, const uint32_t* row_ptr, 
 // The FP64 form's pair cache (see sweep_dev.cuh); hid null: no cache.
 struct PairCache {
   const uint32_t* hid;  // per CSR entry: half-edge id of its pair
-  double4_32a* keep;    // per half-edge: {1 - P_ij, x} at the step's start spins, then the two
-                        // after the move of the endpoint decided first
-  double2* keepl;       // per half-edge: {1 - P_ij, x} after the move of the one decided last
-  uint8_t* upd;         // per site in this MC step: 0 not decided, 1 rejected, 2 accepted
-  int carry;            // the next step uses this graph again: the last endpoint writes keepl
+  double4_32a* keep;    // per half-edge: the two halves of SwitchBufs::keep
+  // per site: bit 2 the parity p_i of its accepted moves since the halves were last written
+  // from the spins (the switch, or cache_build_run), bits 0-1 its decision in this MC step
+  // (0 not decided, 1 rejected, 2 accepted); an accepted move flips p_i as it is decided.  The
+  // current terms of pair (i, j) are in half p_i ^ p_j (0 after a reset): a site reads that
+  // half and writes its proposed-spin terms into the other, so an acceptance flips the half.
+  uint8_t* upd;
+  int carry;  // the next step uses this graph again: the endpoint decided last writes too
+  int reset;  // the halves were written from the spins: every parity starts at 0
 };
 cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32,
                       const uint32_t* row_ptr, const uint32_t* col, const uint32_t* perm,
@@ -162,11 +165,8 @@ cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32
                       uint8_t* acc, uint32_t* defer, uint32_t* dcnt, double4_32a* prop,
                       DevCounters* cnt, const PairCache& pc, cudaStream_t st,
                       int64_t* launches);
-// Between two MC steps on the same graph: carry the pair cache to the current spins (from the
-// last step's decisions), or rebuild it from the spins (after they changed outside the sweep).
-cudaError_t cache_carry_run(const DevParams& P, const SwitchBufs& b, const uint32_t* colour,
-                            const uint8_t* upd, const DevCounters* cnt, cudaStream_t st,
-                            int64_t* launches);
+// Between two MC steps on the same graph after the spins changed outside the sweep: the pair
+// cache rebuilt from the spins (first halves; the next sweep resets the parities).
 cudaError_t cache_build_run(const DevParams& P, const Table& t, const double* s,
                             const SwitchBufs& b, const DevCounters* cnt, cudaStream_t st,
                             int64_t* launches);

@@ -12,13 +12,14 @@ namespace sco {
 namespace {
 
 // Draws the proposal of every site for MC step `step` (see take_proposal); with the pair cache,
-// marks every site as not decided yet in this step.
+// marks every site as not decided yet in this step, keeping its acceptance parity unless the
+// cache was just written from the spins (reset).
 __global__ void __launch_bounds__(256) k_propose(const DevParams P, uint64_t step,
                                                  double4_32a* __restrict__ prop,
-                                                 uint8_t* __restrict__ upd) {
+                                                 uint8_t* __restrict__ upd, int reset) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= P.N) return;
-  if (upd) upd[i] = 0;
+  if (upd) upd[i] = reset ? 0 : upd[i] & 4u;
   SiteCtx c;
   c.i = i;
   const bool ok = propose(P, c, step);
@@ -55,15 +56,16 @@ __global__ void __launch_bounds__(128, 8) k_sweep(const DevParams P, const Sw64*
        idx += gridDim.x * blockDim.x) {
     SiteCtx c;
     load_site(P, c, perm[idx], s);
+    const uint32_t ui = CACHE ? pc.upd[c.i] : 0u;
     if (!take_proposal(c, prop)) {
       acc[c.i] = 0;
-      if (CACHE) pc.upd[c.i] = 1;
+      if (CACHE) pc.upd[c.i] = upd_decided(ui, false);
       continue;
     }
     int d = 1;
     if (CACHE) {
       // evaluated also when u = 0 (accepted outright): the proposed-spin terms must be written
-      d = accept_fp64_cached(P, c, sw, s, row_ptr, col, pc);
+      d = accept_fp64_cached(P, c, sw, s, row_ptr, col, pc, ui);
       if (c.u == 0.0) d = 1;
     } else if (c.u != 0.0) {
       d = PREC == 1 ? accept_fp32(P, c, sw32, s32, row_ptr, col)
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(128, 8) k_sweep(const DevParams P, const Sw64*
       continue;
     }
     write_site(P, c, d == 1, s, PREC == 1 ? s32 : nullptr, acc);
-    if (CACHE) pc.upd[c.i] = d == 1 ? 2 : 1;
+    if (CACHE) pc.upd[c.i] = upd_decided(ui, d == 1);
   }
   nd = warp_sum_u64(nd);
   if ((threadIdx.x & 31) == 0 && nd) {
@@ -109,10 +111,11 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
   for (uint32_t q = warp; q < n; q += nwarps) {
     SiteCtx c;
     load_site(P, c, whole ? perm[b + q] : defer[b + q], s);
+    const uint32_t ui = cache ? pc.upd[c.i] : 0u;
     if (!take_proposal(c, prop)) {  // only a whole-class site can lack a move
       if (lane == 0) {
         acc[c.i] = 0;
-        if (cache) pc.upd[c.i] = 1;
+        if (cache) pc.upd[c.i] = upd_decided(ui, false);
       }
       __syncwarp();
       continue;
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
     if (cache && whole) {
       // the proposed-spin terms are written even when u = 0 accepts outright (deferred sites
       // had them written by k_sweep)
-      d = accept_fp64_warp_cached(P, c, sw, s, row_ptr, col, pc, lane);
+      d = accept_fp64_warp_cached(P, c, sw, s, row_ptr, col, pc, ui, lane);
       if (c.u == 0.0) d = 1;
     } else if (whole && c.u == 0.0) {
       d = 1;
@@ -134,58 +137,12 @@ __global__ void __launch_bounds__(128) k_resolve(const DevParams P, const Sw64* 
     }
     if (lane == 0) {
       write_site(P, c, d == 1, s, fp32_screened ? s32 : nullptr, acc);
-      if (cache) pc.upd[c.i] = d == 1 ? 2 : 1;
+      if (cache) pc.upd[c.i] = upd_decided(ui, d == 1);
     }
     __syncwarp();
   }
   // deferred FP64-form sites were counted by k_sweep already
   if (lane == 0 && ndd && (fp32_screened || whole)) atomicAdd(&cnt->guard_fp64, ndd);
-}
-
-// Pair cache between two MC steps on the same graph: the values of every pair at the current
-// spins are keepl (the later endpoint moved), else the record's second half (only the earlier
-// one moved), else its unchanged first half.  One thread per site over its half-edges (slots),
-// then the overflow list.
-__device__ __forceinline__ void cache_carry(uint32_t i, uint32_t jv, uint32_t h,
-                                            const uint32_t* __restrict__ colour,
-                                            const uint8_t* __restrict__ upd, double4_32a* keep,
-                                            const double2* __restrict__ keepl) {
-  if (jv & kExchOnly) return;
-  const uint32_t j = jv & kIndexMask;
-  const bool i_first = colour[i] < colour[j];
-  const uint32_t ue = upd[i_first ? i : j], ul = upd[i_first ? j : i];
-  double2* r = reinterpret_cast<double2*>(&keep[h]);
-  if (ul == 2u) r[0] = keepl[h];
-  else if (ue == 2u) r[0] = r[1];
-}
-
-__global__ void __launch_bounds__(256) k_cache_carry(int64_t N, const uint32_t* __restrict__ hslot,
-                                                     const uint32_t* __restrict__ hcnt,
-                                                     const uint32_t* __restrict__ colour,
-                                                     const uint8_t* __restrict__ upd,
-                                                     double4_32a* keep,
-                                                     const double2* __restrict__ keepl) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const uint32_t n = min(hcnt[i], (uint32_t)kSlotCap);
-  for (uint32_t q = 0; q < n; ++q) {
-    const uint32_t h = (uint32_t)i * (uint32_t)kSlotCap + q;
-    cache_carry((uint32_t)i, hslot[h], h, colour, upd, keep, keepl);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_cache_carry_ovf(uint32_t N, const uint32_t* __restrict__ ovf,
-                                                         const DevCounters* __restrict__ cnt,
-                                                         uint32_t ovf_cap,
-                                                         const uint32_t* __restrict__ colour,
-                                                         const uint8_t* __restrict__ upd,
-                                                         double4_32a* keep,
-                                                         const double2* __restrict__ keepl) {
-  const unsigned long long n = min(cnt->ovf_n, (unsigned long long)ovf_cap);
-  for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
-       q += (unsigned long long)gridDim.x * blockDim.x)
-    cache_carry(ovf[2 * q], ovf[2 * q + 1], N * (uint32_t)kSlotCap + (uint32_t)q, colour, upd, keep,
-                keepl);
 }
 
 // Pair cache from scratch at the current spins (after the spins changed outside the sweep): the
@@ -230,17 +187,6 @@ __global__ void __launch_bounds__(256) k_cache_build(const DevParams P, const Sw
 
 }  // namespace
 
-cudaError_t cache_carry_run(const DevParams& P, const SwitchBufs& b, const uint32_t* colour,
-                            const uint8_t* upd, const DevCounters* cnt, cudaStream_t st,
-                            int64_t* launches) {
-  const unsigned nb = (unsigned)((P.N + 255) / 256);
-  k_cache_carry<<<nb, 256, 0, st>>>(P.N, b.hslot, b.hcnt, colour, upd, b.keep, b.keepl);
-  k_cache_carry_ovf<<<(unsigned)(2 * num_sms()), 256, 0, st>>>(
-      (uint32_t)P.N, b.ovf, cnt, b.ovf_cap, colour, upd, b.keep, b.keepl);
-  *launches += 2;
-  return cudaGetLastError();
-}
-
 cudaError_t cache_build_run(const DevParams& P, const Table& t, const double* s,
                             const SwitchBufs& b, const DevCounters* cnt, cudaStream_t st,
                             int64_t* launches) {
@@ -259,7 +205,8 @@ cudaError_t sweep_run(const DevParams& P, const Table& t, double* s, float4* s32
   cudaError_t e = cudaMemsetAsync(dcnt, 0, (size_t)g * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const bool cache = precision == 0 && pc.hid != nullptr;
-  k_propose<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P, step, prop, cache ? pc.upd : nullptr);
+  k_propose<<<(unsigned)((P.N + 255) / 256), 256, 0, st>>>(P, step, prop, cache ? pc.upd : nullptr,
+                                                           pc.reset);
   ++*launches;
   const unsigned nres = (unsigned)(4 * num_sms());
   // one launch per colour in ascending order; a class holds about N / g sites.  The grid is a

@@ -144,18 +144,25 @@ __device__ __forceinline__ int accept_fp64(const DevParams& P, const SiteCtx& c,
 }
 
 // The pair cache of the FP64 form (single lattice).  For every surviving dipolar pair (half-edge
-// id h, carried by both CSR entries of the pair) the first half of record keep[h] holds
-// {1 - P = -expm1(x), x = beta (V - Vmax)} of the pair at the spins of the MC step's start (the
-// switch leaves its FP64 values there), each with the error of any FP64 evaluation of it
+// id h, carried by both CSR entries of the pair) record keep[h] holds two halves of
+// {1 - P = -expm1(x), x = beta (V - Vmax)}, each with the error of any FP64 evaluation of it
 // (|x error| <= c0 + 2^-52 |x|, relative error of the elementary function within
-// kExpm1RelErr6).  While a site is decided it writes the pair at its proposed spin: into the
-// record's second half when the other endpoint comes later in the step, into keepl[h] (only
-// when the graph serves the next step too) when it came earlier; upd[i] records that site i is
-// done (1 rejected, 2 accepted).  So the old-spin pair values are the record's first half, or
-// its second half when the earlier endpoint moved: one of the two expm1 evaluations and one of
-// the two dot products per pair endpoint are read instead of computed.  A written 1 - P <= 0
-// (the proposed x not strictly negative in FP64) makes every reader leave its decision to the
-// double-double path, which does not use the cache.
+// kExpm1RelErr6).  Half p_i ^ p_j holds the pair at the current spins, p_i being the parity of
+// site i's accepted moves since the switch (which leaves its FP64 values in the first half) or
+// a rebuild (PairCache::upd).  While a site is decided it reads that half and writes the pair
+// at its proposed spin into the other one: an acceptance flips its parity and so makes the
+// written half the current one, a rejection leaves the read half current.  The endpoint decided
+// last writes only when the next MC step keeps the graph.  So per pair endpoint one of the two
+// expm1 evaluations and one of the two dot products are read instead of computed, and nothing
+// has to be carried between the steps of an epoch.  A written 1 - P <= 0 (the proposed x not
+// strictly negative in FP64) makes every reader leave its decision to the double-double path,
+// which does not use the cache.
+
+// The site's PairCache::upd byte after its decision: an acceptance flips the parity (bit 2).
+__device__ __forceinline__ uint8_t upd_decided(uint32_t ui, bool accepted) {
+  return (uint8_t)(accepted ? ((ui & 4u) ^ 4u) | 2u : (ui & 4u) | 1u);
+}
+
 // accept_fp64 with the old-spin terms from the pair cache; writes the proposed-spin term of
 // every pair (the loop visits every pair, also when the decision is already undecided).
 __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const SiteCtx& c,
@@ -163,7 +170,7 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
                                                   const double* __restrict__ s,
                                                   const uint32_t* __restrict__ row_ptr,
                                                   const uint32_t* __restrict__ col,
-                                                  const PairCache& pc) {
+                                                  const PairCache& pc, uint32_t ui) {
   const double S0 = c.S[0], S1 = c.S[1], S2 = c.S[2];
   const double N0 = c.Sn[0], N1 = c.Sn[1], N2 = c.Sn[2];
   double bdv = 0.0, pz_o = 1.0, pz_n = 1.0;
@@ -186,8 +193,11 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
     const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
     const double a1 = t.a1, bvm = t.bvm;
     const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
-    // {1 - P, x} of the pair at the old spin: one 16-byte read of the record's sector
-    const double2 kv = reinterpret_cast<const double2*>(&pc.keep[h])[uj == 2u ? 1 : 0];
+    // {1 - P, x} of the pair at the old spin: one 16-byte read of the record's sector, from
+    // the half given by the two parities (j's flipped already if it moved in this step)
+    double2* rec = reinterpret_cast<double2*>(&pc.keep[h]);
+    const uint32_t hf = ((ui ^ uj) >> 2) & 1u;
+    const double2 kv = rec[hf];
     const double zo = kv.x, xo = kv.y;
     // x = a1 (S'.S_j) - (S_j.a3 d)(S'.d) - bvm for the proposed spin S'
     const double ns = N0 * bx + N1 * by + N2 * bz;
@@ -196,8 +206,7 @@ __device__ __forceinline__ int accept_fp64_cached(const DevParams& P, const Site
     const double xn = fma(a1, ns, fma(-tp, nd, -bvm));
     const bool okn = neg_strict(xn);
     const double zn = okn ? neg_expm1_np6(xn) : -1.0;
-    if (uj == 0u) reinterpret_cast<double2*>(&pc.keep[h])[1] = make_double2(zn, xn);
-    else if (pc.carry) pc.keepl[h] = make_double2(zn, xn);
+    if ((uj & 3u) == 0u || pc.carry) rec[hf ^ 1u] = make_double2(zn, xn);
     // the cached term must be a positive number (a non-positive one marks an FP64 evaluation
     // that could not be trusted)
     if (!okn || !neg_strict(xo) || !(pos_bits(zo) - 1ull < 0x7FEFFFFFFFFFFFFFull)) {
@@ -538,7 +547,7 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
                                        const double* __restrict__ s,
                                        const uint32_t* __restrict__ row_ptr,
                                        const uint32_t* __restrict__ col, const PairCache& pc,
-                                       int lane) {
+                                       uint32_t ui, int lane) {
   double bdv = 0.0, pz_o = 1.0, pz_n = 1.0, c0s = 0.0;
   int sc_o = 0, sc_n = 0, n = 0, bad = 0, dmax = -2046;
   const uint32_t e1 = row_ptr[c.i + 1];
@@ -555,7 +564,9 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
     const double fx = flip_if(t.ax, dx < 0), fy = flip_if(t.ay, dy < 0);
     const double ax3 = flip_if(t.a3x, dx < 0), ay3 = flip_if(t.a3y, dy < 0);
     const double bx = s[j], by = s[P.N + j], bz = s[2 * P.N + j];
-    const double2 kv = reinterpret_cast<const double2*>(&pc.keep[h])[uj == 2u ? 1 : 0];
+    double2* rec = reinterpret_cast<double2*>(&pc.keep[h]);
+    const uint32_t hf = ((ui ^ uj) >> 2) & 1u;
+    const double2 kv = rec[hf];
     const double zo = kv.x, xo = kv.y;
     const double ns = c.Sn[0] * bx + c.Sn[1] * by + c.Sn[2] * bz;
     const double tp = bx * ax3 + by * ay3;
@@ -563,8 +574,7 @@ __device__ int accept_fp64_warp_cached(const DevParams& P, const SiteCtx& c,
     const double xn = fma(t.a1, ns, fma(-tp, nd, -t.bvm));
     const bool okn = neg_strict(xn);
     const double zn = okn ? neg_expm1_np6(xn) : -1.0;
-    if (uj == 0u) reinterpret_cast<double2*>(&pc.keep[h])[1] = make_double2(zn, xn);
-    else if (pc.carry) pc.keepl[h] = make_double2(zn, xn);
+    if ((uj & 3u) == 0u || pc.carry) rec[hf ^ 1u] = make_double2(zn, xn);
     if (!okn || !neg_strict(xo) || !(pos_bits(zo) - 1ull < 0x7FEFFFFFFFFFFFFFull)) {
       bad = 1;
       continue;

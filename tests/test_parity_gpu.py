@@ -307,3 +307,15 @@ def test_fp64_pair_cache_paths_bit_exact():
         assert np.array_equal(g.spins(), o.spins())
     og, oo = g.observables(), o.observables()
     _same_energy(og["e_switched"], oo["e_switched"], g.N)
+
+
+def test_fp64_pair_cache_carry_thread_path():
+    """The carried pair terms through the one-thread-per-site sweep (classes above 4096 sites):
+    L = 384 with n_sw = 4, two epochs, accept bits and spins equal to the oracle's."""
+    g, o = _pair(384, T=0.6, seed=21, n_sw=4)
+    for k in range(8):
+        g.sweep(1)
+        o.sweep(1)
+        assert np.array_equal(g.accepts(), o.accepts()), k
+    assert np.array_equal(g.spins(), o.spins())
+
