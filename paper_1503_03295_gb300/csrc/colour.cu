@@ -322,10 +322,10 @@ cudaError_t low_setup(uint32_t gcap, int* blocks_per_sm, uint32_t* ecap) {
 
 }  // namespace
 
-// The split record build: row entries read per chunk, and the blocks per SM its registers
-// are held to (16 and 4 measured best at L = 2304: colour 7.35 ms per step, against 7.45 for 8
-// and 6 and 7.83 for 8 and 8, and 7.54 with the records built inside the cooperative kernel).
-constexpr int kRecChunk = 16, kRecBlocks = 4;
+// Blocks per SM of the split record build (k_kw_recw, 39 registers at 6).  Its warp-wide row
+// reads took the records from 2.94 to 2.67 ms per step at L = 2304 against the thread-per-vertex
+// build (16 entries per chunk, 4 blocks).
+constexpr int kRecWBlocks = 6;
 
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
                    uint32_t g, int variant, ColourBufs& b, DevCounters* cnt,
@@ -427,17 +427,17 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     static int rbps = 0;
     if (rbps == 0) {
       if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-               &rbps, k_kw_rec<kRecChunk, kRecBlocks>, 256, 0)) != cudaSuccess)
+               &rbps, k_kw_recw<kRecWBlocks>, 256, 0)) != cudaSuccess)
         return e;
       if (rbps < 1) rbps = 1;
     }
     const int64_t sgrid = std::min<int64_t>((int64_t)rbps * num_sms(), kKwSplitBlocks);
     if (b.boff && g <= kLowMaxPal) {
-      // per level: the records in two plain launches (k_kw_hist reserves, k_kw_rec builds),
+      // per level: the records in two plain launches (k_kw_hist reserves, k_kw_recw builds),
       // then the cooperative kernel runs that level's buckets alone
       for (unsigned p = low + 1; p <= M; ++p) {
         k_kw_hist<<<(unsigned)sgrid, 256, 0, st>>>(V, p, b.boff);
-        k_kw_rec<kRecChunk, kRecBlocks><<<(unsigned)sgrid, 256, 0, st>>>(V, p, b.boff);
+        k_kw_recw<kRecWBlocks><<<(unsigned)sgrid, 256, 0, st>>>(V, p, b.boff);
         V.p_only = p;
         V.prebuilt = 1;
         e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr<true>,

@@ -54,7 +54,7 @@ struct KwView {
   // them, each item waiting for its listed larger neighbours; 0: a quarter of the grid
   uint32_t free_max;
   // split record build (one lattice): run level p_only alone (0: every level), and with
-  // prebuilt its buckets, list and records come from k_kw_hist and k_kw_rec
+  // prebuilt its buckets, list and records come from k_kw_hist and k_kw_recw
   unsigned p_only;
   int prebuilt;
 };
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(256, kBuckets ? kBcrBucketBlocks : 3) k_kw_bcr
 // Split record build of level p for one lattice (V.R == 1), ahead of a k_kw_bcr launch that
 // runs only that level's buckets.  Both kernels deal the right-half slots to their threads in
 // the same grid-stride order, so that the reservation each block of k_kw_hist makes per colour
-// is where k_kw_rec puts that block's items; inside a (block, colour) range the order is free
+// is where k_kw_recw puts that block's items; inside a (block, colour) range the order is free
 // (a bucket's vertices share a colour, hence no edge).  A plain launch with more resident
 // threads than the cooperative kernel keeps more records' load chains in flight.
 __device__ __forceinline__ uint32_t kw_split_slots(const RepPlan& pl, uint32_t N, unsigned p) {
@@ -545,11 +545,23 @@ __global__ void __launch_bounds__(256) k_kw_hist(const KwView V, unsigned p,
     boff[(size_t)blockIdx.x * pal + c] = hist[c] ? atomicAdd(&bc[c], hist[c]) : 0u;
 }
 
-template <int kChunk, int kMinBlocks>
-__global__ void __launch_bounds__(256, kMinBlocks) k_kw_rec(const KwView V, unsigned p,
-                                                            const uint32_t* __restrict__ boff) {
+// The records of level p (kw_item_build's), with the rows read by whole warps: the warp's 32
+// slots are consecutive vertices of one right half (or of two), so their rows are one contiguous
+// run of col, which the lanes read 32 entries at a time, each entry by one lane (coalesced).  A lane finds its entry's vertex in the warp's row prefix (in shared
+// memory), classifies the neighbour as kw_item_build does, and adds it to that vertex's record: a
+// left-half colour by an atomic OR into the vertex's mask, a larger right-half one into the list
+// at the vertex's count plus its rank among the vertex's list entries of the round.  Grid and
+// slot order as in k_kw_hist (its reservations hold).
+template <int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) k_kw_recw(const KwView V, unsigned p,
+                                                             const uint32_t* __restrict__ boff) {
+  constexpr int kW = 8;           // warps per block
+  constexpr int kRecRounds = 4;   // rounds of 32 row entries loaded together
   __shared__ uint32_t start[kLowMaxPal + 1];
   __shared__ uint32_t lcur[kLowMaxPal];
+  __shared__ uint32_t w_pre[kW][33];
+  __shared__ uint32_t w_rb[kW][32], w_lo[kW][32], w_c[kW][32], w_pos[kW][32], w_n[kW][32];
+  __shared__ uint32_t w_m[kW][2][32];
   const RepPlan pl = V.plan[0];
   const uint32_t N = V.site_start[1] - V.site_start[0];
   const unsigned pal = V.pal;
@@ -563,14 +575,106 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_kw_rec(const KwView V, unsi
   for (unsigned c = threadIdx.x; c < pal; c += blockDim.x)
     start[c] += boff[(size_t)blockIdx.x * pal + c];
   __syncthreads();
+  const uint32_t gsz = pl.g << p, half = pl.g << (p - 1);
   const uint32_t Rtot = kw_split_slots(pl, N, p), nth = gridDim.x * blockDim.x;
-  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < Rtot; slot += nth) {
-    const uint32_t v = kw_vertex(slot, pl.g << (p - 1), p, pl.magic);
-    if (v >= N) continue;
-    const uint32_t c = V.col8[v];
-    const uint32_t pos = start[c] + atomicAdd(&lcur[c], 1u);
-    V.list[pos] = v;
-    kw_item_build<kChunk>(V, pos, v, 0u, c, p, pl);
+  const int w = threadIdx.x >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
+  const uint32_t* __restrict__ col = V.col;
+  const uint8_t* __restrict__ col8 = V.col8;
+  uint32_t* pre = w_pre[w];
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < Rtot; base += nth) {
+    const uint32_t slot = base + lane;
+    uint32_t v = kNone, len = 0;
+    if (slot < Rtot) {
+      const uint32_t vv = kw_vertex(slot, half, p, pl.magic);
+      if (vv < N) {
+        v = vv;
+        const uint32_t c = col8[v];
+        const uint32_t pos = start[c] + atomicAdd(&lcur[c], 1u);
+        V.list[pos] = v;
+        const uint32_t rb = V.row_ptr[v];
+        len = V.row_ptr[v + 1] - rb;
+        w_rb[w][lane] = rb;
+        w_lo[w][lane] = (fdiv(v, pl.magic) >> p) * gsz;
+        w_c[w][lane] = c;
+        w_pos[w][lane] = pos;
+      }
+    }
+    w_n[w][lane] = 0;
+    w_m[w][0][lane] = 0;
+    w_m[w][1][lane] = 0;
+    uint32_t incl = len;  // inclusive prefix of the row lengths over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += t;
+    }
+    pre[lane + 1] = incl;
+    if (lane == 0) pre[0] = 0;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    uint32_t k = 0;  // the vertex (lane) of this lane's entry, nondecreasing over the rounds
+    for (uint32_t t0 = 0; t0 < total; t0 += 32 * kRecRounds) {
+      // kRecRounds rounds at a time: their row entries, then their neighbours' colours, are
+      // loaded together
+      uint32_t kk[kRecRounds], uu[kRecRounds], cu[kRecRounds];
+#pragma unroll
+      for (int r = 0; r < kRecRounds; ++r) {
+        const uint32_t t = t0 + 32 * r + lane;
+        kk[r] = 0;
+        uu[r] = kNone;
+        if (t < total) {
+          while (pre[k + 1] <= t) ++k;
+          kk[r] = k;
+          uu[r] = col[w_rb[w][k] + (t - pre[k])];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kRecRounds; ++r) {
+        cu[r] = 0;
+        if (uu[r] != kNone) {
+          uu[r] = (uu[r] & kIndexMask) - w_lo[w][kk[r]];
+          if (uu[r] < gsz) cu[r] = col8[w_lo[w][kk[r]] + uu[r]];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kRecRounds; ++r) {
+        const uint32_t tr = t0 + 32 * r, t = tr + lane;
+        if (tr >= total) break;  // uniform
+        const bool act = t < total;
+        const uint32_t kr = kk[r], u = uu[r];
+        bool inl = false;
+        uint32_t seg = 0;
+        if (act) {
+          if (u < gsz) {
+            if (u < half) atomicOr(&w_m[w][cu[r] >> 5][kr], 1u << (cu[r] & 31));
+            else if (cu[r] > w_c[w][kr]) inl = true;
+          }
+          seg = pre[kr] > tr ? pre[kr] - tr : 0;  // first lane of vertex kr in this round
+        }
+        const uint32_t lm = __ballot_sync(0xffffffffu, inl);
+        const uint32_t mine = lm & ~((1u << seg) - 1u);  // list entries of lanes >= seg
+        uint32_t n0 = 0;
+        if (act) n0 = w_n[w][kr];
+        if (inl) {
+          const uint32_t n = n0 + __popc(mine & lt);
+          if (n < (uint32_t)kItemList)
+            V.ilist[(size_t)w_pos[w][kr] * kItemList + n] = w_lo[w][kr] + u;
+        }
+        __syncwarp();
+        // the last lane of vertex kr in this round adds the round's list entries to its count
+        if (act && (t + 1 == pre[kr + 1] || lane == 31))
+          w_n[w][kr] = n0 + __popc(mine & (lt | (1u << lane)));
+        __syncwarp();
+      }
+    }
+    if (v != kNone) {
+      const uint32_t pos = w_pos[w][lane], n = w_n[w][lane];
+      V.imask[pos] = (unsigned long long)w_m[w][0][lane] | ((unsigned long long)w_m[w][1][lane] << 32);
+      V.imeta[pos] = n > (uint32_t)kItemList ? kItemSlow : n;
+    }
+    __syncwarp();
   }
 }
 
