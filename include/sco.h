@@ -199,8 +199,8 @@ sco_status sco_get_timing(sco_ctx* c, double ms[3], int64_t calls[3]);
  * n <= SCO_KW_STATIC_MAX_VERTICES (8 MiB + 512 B, held on every device that loads the
  * library until the process exits); larger n returns SCO_EINVAL before any device work.
  * The first call on a device also does a one-time set-up with that device current: it
- * looks up that array's device address (cudaGetSymbolAddress) and the launch occupancy;
- * make that first call before any stream capture begins.  Every call reuses the same array
+ * looks up that array's device address (cudaGetSymbolAddress) and the launch occupancy.
+ * Every call reuses the same array
  * (the control block is cleared on each call), so calls that overlap on the GPU, from any
  * stream or thread, race: serialise them.  Every call copies max_degree and t_R back to the
  * host and synchronises `stream` before it returns; it returns SCO_ETIMEOUT if a bounded
