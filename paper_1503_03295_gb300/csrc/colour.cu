@@ -322,10 +322,14 @@ cudaError_t low_setup(uint32_t gcap, int* blocks_per_sm, uint32_t* ecap) {
 
 }  // namespace
 
-// Blocks per SM of the split record build (k_kw_recw, 39 registers at 6).  Its warp-wide row
-// reads took the records from 2.94 to 2.67 ms per step at L = 2304 against the thread-per-vertex
-// build (16 entries per chunk, 4 blocks).
+// The split record build of a grid-wide level: k_kw_recw (warp-wide row reads; 6 blocks per SM
+// at 39 registers) once a level-p group spans at least kRecWarpRows lattice rows, else k_kw_rec
+// (a thread per vertex, 16 entries per chunk, 4 blocks per SM).  Per level at L = 2304 (g = 39)
+// the thread kernel took 149, 192, 227, 255 ... 309 us for levels 7, 8, 9, 10 ... 17 (groups of
+// 2.2, 4.3, 8.7, 17.3 ... rows), the warp kernel 237-249 us at every level.
+constexpr int kRecChunk = 16, kRecBlocks = 4;
 constexpr int kRecWBlocks = 6;
+constexpr uint64_t kRecWarpRows = 12;
 
 cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* col,
                    uint32_t g, int variant, ColourBufs& b, DevCounters* cnt,
@@ -424,20 +428,31 @@ cudaError_t kw_run(const DevParams& P, const uint32_t* row_ptr, const uint32_t* 
     // threads' polling slows the recolouring ones)
     V.free_max = 0;
     void* args[] = {(void*)&V};
-    static int rbps = 0;
+    static int rbps = 0, tbps = 0;
     if (rbps == 0) {
       if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                &rbps, k_kw_recw<kRecWBlocks>, 256, 0)) != cudaSuccess)
         return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &tbps, k_kw_rec<kRecChunk, kRecBlocks>, 256, 0)) != cudaSuccess)
+        return e;
       if (rbps < 1) rbps = 1;
+      if (tbps < 1) tbps = 1;
     }
-    const int64_t sgrid = std::min<int64_t>((int64_t)rbps * num_sms(), kKwSplitBlocks);
+    const int64_t wgrid = std::min<int64_t>((int64_t)rbps * num_sms(), kKwSplitBlocks);
+    const int64_t tgrid = std::min<int64_t>((int64_t)tbps * num_sms(), kKwSplitBlocks);
     if (b.boff && g <= kLowMaxPal) {
       // per level: the records in two plain launches (k_kw_hist reserves, k_kw_recw builds),
       // then the cooperative kernel runs that level's buckets alone
       for (unsigned p = low + 1; p <= M; ++p) {
-        k_kw_hist<<<(unsigned)sgrid, 256, 0, st>>>(V, p, b.boff);
-        k_kw_recw<kRecWBlocks><<<(unsigned)sgrid, 256, 0, st>>>(V, p, b.boff);
+        // both launches of a level take the same grid (k_kw_hist's reservations are per block)
+        const bool wide = ((uint64_t)g << p) >= kRecWarpRows * (uint64_t)P.Lx;
+        const unsigned sgrid = (unsigned)(wide ? wgrid : tgrid);
+        k_kw_hist<<<sgrid, 256, 0, st>>>(V, p, b.boff);
+        if (wide)
+          k_kw_recw<kRecWBlocks><<<sgrid, 256, 0, st>>>(V, p, b.boff);
+        else
+          k_kw_rec<kRecChunk, kRecBlocks><<<sgrid, 256, 0, st>>>(V, p, b.boff);
         V.p_only = p;
         V.prebuilt = 1;
         e = cudaLaunchCooperativeKernel((const void*)k_kw_bcr<true>,

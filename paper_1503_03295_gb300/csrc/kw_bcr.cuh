@@ -549,6 +549,38 @@ __global__ void __launch_bounds__(256) k_kw_hist(const KwView V, unsigned p,
     boff[(size_t)blockIdx.x * pal + c] = hist[c] ? atomicAdd(&bc[c], hist[c]) : 0u;
 }
 
+// The records of level p, one thread per right-half vertex walking its own row (kw_item_build,
+// kChunk entries at a time).  Cheaper than k_kw_recw at the low grid-wide levels, where most of a
+// row leaves the vertex's group and is skipped after one compare.
+template <int kChunk, int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) k_kw_rec(const KwView V, unsigned p,
+                                                            const uint32_t* __restrict__ boff) {
+  __shared__ uint32_t start[kLowMaxPal + 1];
+  __shared__ uint32_t lcur[kLowMaxPal];
+  const RepPlan pl = V.plan[0];
+  const uint32_t N = V.site_start[1] - V.site_start[0];
+  const unsigned pal = V.pal;
+  const uint32_t* bc = V.bcnt + (size_t)p * pal;
+  for (unsigned c = threadIdx.x; c < pal; c += blockDim.x) {
+    start[c] = bc[c];
+    lcur[c] = 0;
+  }
+  __syncthreads();
+  block_scan_excl(start, (int)pal);
+  for (unsigned c = threadIdx.x; c < pal; c += blockDim.x)
+    start[c] += boff[(size_t)blockIdx.x * pal + c];
+  __syncthreads();
+  const uint32_t Rtot = kw_split_slots(pl, N, p), nth = gridDim.x * blockDim.x;
+  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < Rtot; slot += nth) {
+    const uint32_t v = kw_vertex(slot, pl.g << (p - 1), p, pl.magic);
+    if (v >= N) continue;
+    const uint32_t c = V.col8[v];
+    const uint32_t pos = start[c] + atomicAdd(&lcur[c], 1u);
+    V.list[pos] = v;
+    kw_item_build<kChunk>(V, pos, v, 0u, c, p, pl);
+  }
+}
+
 // The records of level p (kw_item_build's), with the rows read by whole warps: the warp's 32
 // slots are consecutive vertices of one right half (or of two), so their rows are one contiguous
 // run of col, which the lanes read 32 entries at a time, each entry by one lane (coalesced).  A lane finds its entry's vertex in the warp's row prefix (in shared
